@@ -1,0 +1,239 @@
+"""FP64 CPU oracle for the preconditioned Legendre-Galerkin solve (arXiv 2004.13961).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the CUDA library in ``paper_2004_13961_gb300`` and neither imports the
+other.  Each wrapper below calls one function of ``lsg_oracle.c``; the C file
+cites the passage of the paper that each one follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lsg_oracle.c")
+_LIB = os.path.join(_HERE, "liblsg_oracle.so")
+
+OR_OK = 0
+OR_ERR_BREAKDOWN = -4
+OR_ERR_NOT_CONVERGED = -5
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, OpenMP over independent loops)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", _LIB, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        ci, cll, cd = ctypes.c_int, ctypes.c_longlong, ctypes.c_double
+        L.or_legendre_all.argtypes = [ci, cd, dp]
+        L.or_legendre_deriv_all.argtypes = [ci, cd, dp]
+        L.or_gauss.argtypes = [ci, dp, dp]
+        L.or_apply_K.argtypes = [ci, ci, ci, dp, dp, dp, dp]
+        L.or_dense_K.argtypes = [ci, ci, ci, dp, dp, dp]
+        L.or_load_vector.argtypes = [ci, ci, ci, dp, dp]
+        L.or_load_vector_legendre.argtypes = [ci, ci, ci, dp, dp]
+        L.or_coef_trunc.argtypes = [ci, ci, ci, dp, dp]
+        L.or_band_matrices.argtypes = [ci, ci, dp, dp]
+        L.or_pattern_nnz.argtypes = [ci, ci, ci, ci]
+        L.or_pattern_nnz.restype = cll
+        L.or_assemble_M.argtypes = [ci, ci, ci, dp, dp, ci, dp, dp, i64p, i32p, dp]
+        L.or_ilu0.argtypes = [cll, i64p, i32p, dp]
+        L.or_ilu_solve.argtypes = [cll, i64p, i32p, dp, dp, dp]
+        L.or_pcg.argtypes = [ci, ci, ci, dp, dp, i64p, i32p, dp, dp, dp, cd, ci,
+                             ctypes.POINTER(ci), dp, dp]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def legendre_all(nmax: int, x: float) -> np.ndarray:
+    out = np.zeros(nmax + 1)
+    lib().or_legendre_all(nmax, float(x), _dp(out))
+    return out
+
+
+def legendre_deriv_all(nmax: int, x: float) -> np.ndarray:
+    out = np.zeros(nmax + 1)
+    lib().or_legendre_deriv_all(nmax, float(x), _dp(out))
+    return out
+
+
+def gauss(Q: int):
+    x = np.zeros(Q)
+    w = np.zeros(Q)
+    rc = lib().or_gauss(Q, _dp(x), _dp(w))
+    assert rc == 0
+    return x, w
+
+
+def _n(d, N):
+    return (N - 1) ** d
+
+
+def apply_K(d, N, Q, a, b, u):
+    a, b, u = _c64(a), _c64(b), _c64(u)
+    y = np.zeros(_n(d, N))
+    rc = lib().or_apply_K(d, N, Q, _dp(a), _dp(b), _dp(u), _dp(y))
+    assert rc == 0, rc
+    return y
+
+
+def dense_K(d, N, Q, a, b):
+    a, b = _c64(a), _c64(b)
+    n = _n(d, N)
+    K = np.zeros((n, n))
+    rc = lib().or_dense_K(d, N, Q, _dp(a), _dp(b), _dp(K))
+    assert rc == 0, rc
+    return K
+
+
+def load_vector(d, N, Q, f):
+    f = _c64(f)
+    F = np.zeros(_n(d, N))
+    rc = lib().or_load_vector(d, N, Q, _dp(f), _dp(F))
+    assert rc == 0, rc
+    return F
+
+
+def load_vector_legendre(d, N, fc):
+    fc = _c64(fc)
+    deg = fc.shape[0] - 1 if fc.ndim else 0
+    F = np.zeros(_n(d, N))
+    rc = lib().or_load_vector_legendre(d, N, deg, _dp(fc.ravel()), _dp(F))
+    assert rc == 0, rc
+    return F
+
+
+def coef_trunc(d, Q, T, c):
+    c = _c64(c)
+    out = np.zeros((T + 1) ** d)
+    rc = lib().or_coef_trunc(d, Q, T, _dp(c), _dp(out))
+    assert rc == 0, rc
+    return out
+
+
+def band_matrices(N, T):
+    n1 = N - 1
+    S = np.zeros((T + 1, n1, n1))
+    M = np.zeros((T + 1, n1, n1))
+    rc = lib().or_band_matrices(N, T, _dp(S), _dp(M))
+    assert rc == 0, rc
+    return S, M
+
+
+class CSR:
+    """Row-compressed matrix with ascending columns (oracle storage of M / ILU(0))."""
+
+    def __init__(self, n, rowptr, col, val):
+        self.n, self.rowptr, self.col, self.val = n, rowptr, col, val
+
+    def to_dense(self):
+        A = np.zeros((self.n, self.n))
+        for i in range(self.n):
+            s, e = self.rowptr[i], self.rowptr[i + 1]
+            A[i, self.col[s:e]] = self.val[s:e]
+        return A
+
+    def get(self, i, j):
+        s, e = self.rowptr[i], self.rowptr[i + 1]
+        idx = np.searchsorted(self.col[s:e], j)
+        if idx < e - s and self.col[s + idx] == j:
+            return self.val[s + idx]
+        return None
+
+    def copy(self):
+        return CSR(self.n, self.rowptr, self.col, self.val.copy())
+
+
+def has_b(b) -> int:
+    return int(np.any(np.asarray(b) != 0.0))
+
+
+def assemble_M(d, N, T, ahat, bhat, hasb, S=None, Mb=None):
+    if S is None:
+        S, Mb = band_matrices(N, T)
+    ahat, bhat = _c64(ahat), _c64(bhat)
+    S, Mb = _c64(S), _c64(Mb)
+    n = _n(d, N)
+    nnz = lib().or_pattern_nnz(d, N, T, int(hasb))
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    col = np.zeros(nnz, dtype=np.int32)
+    val = np.zeros(nnz)
+    rc = lib().or_assemble_M(d, N, T, _dp(ahat), _dp(bhat), int(hasb), _dp(S), _dp(Mb),
+                             rowptr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                             col.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(val))
+    assert rc == 0, rc
+    return CSR(n, rowptr, col, val)
+
+
+def ilu0(M: CSR):
+    H = M.copy()
+    rc = lib().or_ilu0(H.n, H.rowptr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                       H.col.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(H.val))
+    return H, rc
+
+
+def ilu_solve(LU: CSR, r):
+    r = _c64(r)
+    z = np.zeros(LU.n)
+    rc = lib().or_ilu_solve(LU.n, LU.rowptr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                            LU.col.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(LU.val),
+                            _dp(r), _dp(z))
+    assert rc == 0
+    return z
+
+
+def setup(d, N, Q, T, a, b):
+    """Preconditioner setup: truncated coefficients, band matrices, M, ILU(0)."""
+    ahat = coef_trunc(d, Q, T, a)
+    bhat = coef_trunc(d, Q, T, b)
+    hb = has_b(b)
+    M = assemble_M(d, N, T, ahat, bhat, hb)
+    LU, rc = ilu0(M)
+    return dict(ahat=ahat, bhat=bhat, M=M, LU=LU, ilu_status=rc, has_b=hb)
+
+
+def pcg(d, N, Q, a, b, LU: CSR, F, eps=1e-12, kmax=10000, x0=None):
+    a, b, F = _c64(a), _c64(b), _c64(F)
+    x = np.zeros(_n(d, N)) if x0 is None else _c64(x0).copy()
+    it = ctypes.c_int(0)
+    rr = np.zeros(1)
+    rt = np.zeros(1)
+    rc = lib().or_pcg(d, N, Q, _dp(a), _dp(b),
+                      LU.rowptr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                      LU.col.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(LU.val),
+                      _dp(F), _dp(x), float(eps), int(kmax), ctypes.byref(it), _dp(rr), _dp(rt))
+    return dict(x=x, iters=it.value, relres=rr[0], relres_true=rt[0], status=rc)
+
+
+def solve(d, N, Q, T, a, b, F, eps=1e-12, kmax=10000):
+    st = setup(d, N, Q, T, a, b)
+    out = pcg(d, N, Q, a, b, st["LU"], F, eps, kmax)
+    out.update(st)
+    return out
