@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark of the preconditioned Legendre-Galerkin solve on one GB300 (or N replicas).
+
+One step = the whole hot path on one synthetic problem: setup from the
+coefficient samples (Gauss tables, truncated series, band matrices, M, ILU(0)),
+the load vector, and PCG (Algorithm 1) to relative residual 1e-12 -- the 2D
+FP64 workload N=512 (261,121 unknowns), T=8, a=exp(g_a), b=exp(g_b) random
+Legendre series (seeds 1, 2), f with random Legendre coefficients (seed 3).
+`value` is solves/s over all ranks with inputs resident in HBM; `e2e` is the
+same through the C ABI with host buffers (copies inside the timed region).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun every rank solves its own replica (independent problems shard
+with no data-path collective: weak scaling); timing is the max over ranks.
+The reference arm (--impl reference) times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s & A*x GDOF/s at rel. residual 1e-10 (mixed vs FP64); p50/p99 latency"
+RTOL = 1e-12
+WORKLOAD = "2d-exp-series N=512 (261,121 unknowns) T=8 Q=514, FP64 PCG+ILU(0) to rel. residual 1e-12"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm, bf16 = 6800.0, 1900.0
+    src = "fallback"
+    if os.path.exists(path):
+        with open(path) as fh:
+            P = json.load(fh)
+        hbm = float(P.get("hbm_gbs", hbm))
+        bf16 = float(P.get("bf16_tflops", bf16))
+        src = "measured"
+    return hbm, bf16, src
+
+
+# FP64 FMA throughput of this machine's GB300 (152 SMs): 1.194 TFLOP/s measured with an
+# 8-chain DFMA loop over 8 CTAs/SM (0.5 of a DFMA per SM per clock at ~1.99 GHz).
+FP64_PEAK_TFLOPS = 1.194
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.out.name)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(smax) if smax else None,
+                    samples=len(sm), reasons=sorted(reasons))
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- oracle (CPU) leg
+
+def oracle_sample(p, iters_hint=None):
+    """Time the CPU oracle on a bounded sample of the workload: the full setup
+    (truncated series, M assembly, ILU(0)) plus two K x and two ILU solves at full
+    size; a solve is extrapolated as setup + iters x (K x + M^-1 r + vector ops)."""
+    import oracle as O
+    d, N, T, Q = p["d"], p["N"], p["T"], p["Q"]
+    t0 = time.perf_counter()
+    ah = O.coef_trunc(d, Q, T, p["a"])
+    bh = O.coef_trunc(d, Q, T, p["b"])
+    M = O.assemble_M(d, N, T, ah, bh, O.has_b(p["b"]))
+    LU, rc = O.ilu0(M)
+    t_setup = time.perf_counter() - t0
+    F = O.load_vector(d, N, Q, p["f"])
+    x = np.random.default_rng(0).standard_normal(len(F))
+    t0 = time.perf_counter()
+    for _ in range(2):
+        O.apply_K(d, N, Q, p["a"], p["b"], x)
+    t_kx = (time.perf_counter() - t0) / 2
+    t0 = time.perf_counter()
+    for _ in range(2):
+        O.ilu_solve(LU, x)
+    t_minv = (time.perf_counter() - t0) / 2
+    iters = iters_hint if iters_hint else 39
+    t_solve = t_setup + iters * (t_kx + t_minv)
+    return dict(t_setup=t_setup, t_kx=t_kx, t_minv=t_minv, iters=iters, t_solve=t_solve,
+                sample_s=t_setup + 2 * (t_kx + t_minv))
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, world, rank):
+    from paper_2004_13961_gb300 import workloads as W
+    if rank != 0:
+        return
+    p = W.exp_2d_n512()
+    for _ in range(args.warmup if args.warmup < 1 else 0):
+        pass
+    times = []
+    info = None
+    for _ in range(max(1, args.steps)):
+        info = oracle_sample(p)
+        times.append(info["t_solve"])
+    t = float(np.mean(times))
+    value = 1.0 / t
+    cb = dict(value=value, unit="solves/s", cores=cores(), kind="oracle",
+              sample=(f"per step: full oracle setup ({info['t_setup']:.1f} s: truncated series, M assembly, "
+                      f"ILU(0)) + 2 K x ({info['t_kx']:.2f} s each) + 2 ILU solves ({info['t_minv']:.2f} s each) "
+                      f"at N=512; solve = setup + {info['iters']} x (K x + M^-1 r)"))
+    line = dict(metric=METRIC, value=value, unit="solves/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=t * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic", impl="reference", config=dict(workload=WORKLOAD),
+                cpu_baseline=cb, e2e=dict(value=value, unit="solves/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- native (GPU) leg
+
+def run_native(args, world, rank, local):
+    import torch
+    from paper_2004_13961_gb300 import lsg
+    from paper_2004_13961_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lsg.load()
+    p = W.exp_2d_n512()
+    d, N, T, Q = p["d"], p["N"], p["T"], p["Q"]
+    a = torch.tensor(p["a"], device=dev)
+    b = torch.tensor(p["b"], device=dev)
+    f = torch.tensor(p["f"], device=dev)
+    n = (N - 1) ** d
+    F = torch.empty(n, dtype=torch.float64, device=dev)
+    u = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2 (129 MB)
+
+    last = {}
+
+    def step():
+        ctx = lsg.Context(d, N, T, a, b, Q=Q)
+        ctx.load_vector(f, F)
+        u.zero_()
+        _, info = ctx.pcg_solve(F, u, rtol=RTOL)
+        last["info"] = info
+        last["ilu_ms"] = ctx.query(lsg.Q_ILU_US) / 1e3
+        last["asm_ms"] = ctx.query(lsg.Q_ASSEMBLE_US) / 1e3
+        ctx.close()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    l0 = lsg.kernel_launches()
+    for k in range(args.steps):
+        flush.fill_(float(k))  # evict L2 between timed steps (outside the events)
+        ev[k][0].record()
+        step()
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    launches = lsg.kernel_launches() - l0
+    clocks = sampler.stop()
+    barrier(world)
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    t_total = max_over_ranks(sum(step_ms) / 1e3, world)
+    value = world * args.steps / t_total
+    info = last["info"]
+
+    # ---- stage breakdown (separate from the timed steps) ----
+    ctx = lsg.Context(d, N, T, a, b, Q=Q)
+    ctx.load_vector(f, F)
+    x = torch.randn(n, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+
+    def evtime(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(reps):
+            fn()
+        e.record()
+        torch.cuda.synchronize()
+        return s.elapsed_time(e) / reps
+
+    t_kx = evtime(lambda: ctx.apply_A(x, y), 20)
+    t_minv = evtime(lambda: ctx.apply_Minv(F, z), 3)
+    ctx.close()
+    hbm, bf16, psrc = peaks()
+    Qh = (Q + 1) // 2
+    n1 = N - 1
+    # algorithmic work, parity-folded transforms (4 contractions of half length):
+    # 2D: (8 n1^2 Q + 12 Q^2 n1) / 2 flops
+    kx_flops = (8.0 * n1 * n1 * Q + 12.0 * Q * Q * n1) / 2.0
+    w = T + 2
+    lower = ((2 * w + 1) ** 2 - 1) // 2
+    sweep_bytes = n * lower * 8 + 3 * n * 8  # factors of one triangle + rhs, out, neighbour reads
+    iters = info["iters"]
+    per_solve = dict(setup_ilu_ms=last["ilu_ms"], setup_assemble_ms=last["asm_ms"],
+                     pcg_kx_ms=iters * t_kx, pcg_minv_ms=iters * t_minv)
+    dominant = max(per_solve, key=per_solve.get)
+    if dominant == "pcg_minv_ms":
+        dur = t_minv / 2.0
+        roof = dict(kernel="k_sweep (one triangular sweep, Alg. 3/4)", bound="hbm", achieved=sweep_bytes / dur / 1e6,
+                    peak=hbm, unit="GB/s", traffic=None)
+    elif dominant == "pcg_kx_ms":
+        dur = t_kx / 4.0
+        roof = dict(kernel="k_xf_fwd/k_xf_bwd (one of 4 FP64 contractions)", bound="alu",
+                    achieved=kx_flops / 4 / dur / 1e9, peak=FP64_PEAK_TFLOPS * 1e3, unit="GFLOP/s", traffic=None)
+    else:
+        dur = last["ilu_ms"]
+        roof = dict(kernel="k_ilu0 (Alg. 2)", bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS * 1e3,
+                    unit="GFLOP/s", traffic=None)
+    if roof["achieved"] is not None:
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["peak_source"] = psrc if roof["bound"] == "hbm" else "measured FP64 FMA loop"
+
+    # ---- e2e: host buffers through the C ABI, copies inside the timed region ----
+    ha, hb, hf = p["a"].copy(), p["b"].copy(), p["f"].copy()
+    hF = np.empty(n)
+    hu = np.empty(n)
+    e2e_t = []
+    for k in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c2 = lsg.Context(d, N, T, ha, hb, Q=Q)
+        c2.load_vector(hf, hF)
+        hu[:] = 0.0
+        c2.pcg_solve(hF, hu, rtol=RTOL)
+        c2.close()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_val = world / max_over_ranks(float(np.mean(e2e_t)), world)
+    nq = Q ** d
+    e2e = dict(value=e2e_val, unit="solves/s", h2d_bytes_per_step=3 * nq * 8 + 2 * n * 8,
+               d2h_bytes_per_step=2 * n * 8)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = oracle_sample(p, iters)
+        cpu = dict(value=1.0 / s["t_solve"], unit="solves/s", cores=cores(), kind="oracle",
+                   sample=(f"full oracle setup ({s['t_setup']:.1f} s) + 2 K x ({s['t_kx']:.2f} s each) + 2 ILU "
+                           f"solves ({s['t_minv']:.2f} s each) at N=512; solve = setup + {iters} x (K x + M^-1 r)"))
+
+    if rank == 0:
+        line = dict(
+            metric=METRIC, value=value, unit="solves/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+            ms_per_step=t_total * 1e3 / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+            dtype="f64", data="synthetic",
+            config=dict(workload=WORKLOAD, l2="256 MB buffer written between timed steps (factors 0.94 GB > L2)",
+                        parallelism=f"replicas x{world}"),
+            kx_gdof_s=n / (t_kx * 1e-3) / 1e9, kx_ms=t_kx, minv_ms=t_minv, pcg_iters=iters,
+            relres_true=info["relres_true"], breakdown_ms=per_solve,
+            roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clocks)
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_native(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

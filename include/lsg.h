@@ -1,0 +1,218 @@
+/*
+ * lsg.h -- C ABI of the GB300 (sm_103a) preconditioned Legendre-Galerkin solver.
+ *
+ * Problem (Diao, Hu & Ma, arXiv 2004.13961, Sec. 3, `NSproblem`):
+ *     -div(a(x) grad u) + b(x) u = f  on (-1,1)^d,  u = 0 on the boundary, d = 1, 2, 3,
+ * with a = beta (diffusion) and b = alpha (reaction) in the paper's notation.
+ * Galerkin basis phi_k = L_k - L_{k+2}, k = 0..N-2, tensor products in 2D/3D
+ * (Sec. 3); the discrete system is K u_hat = F with K = A + B
+ * (Sec. 3, `algebraicsystem`), where A and B are applied matrix-free by
+ * Legendre-Gauss quadrature (Sec. 4.3, "fast matrix-vector multiplications").
+ * The preconditioner M replaces a and b by their Legendre series truncated to
+ * degree T in each direction (Sec. 4.1, `1DM`, `2DM`, `3DM`) and is applied
+ * through its ILU(0) factors (Sec. 4.2, Algorithms 2-4) inside PCG
+ * (Sec. 4, Algorithm 1).
+ *
+ * Layout contract (Sec. 3, unknown ordering):
+ *   - coefficient vectors (u_hat, F, x, y, r, z) hold n = (N-1)^d FP64 values,
+ *     first index fastest: u_hat[k + (N-1) j + (N-1)^2 l] multiplies
+ *     phi_k(x) phi_j(y) phi_l(z);
+ *   - grid arrays (samples of a, b, f; lsg_eval output) hold Q^d FP64 values at
+ *     the tensor Legendre-Gauss grid, nodes ascending (lsg_gauss), x fastest.
+ *
+ * Pointers: every array argument may be a host pointer or a device pointer of
+ * the current CUDA device (detected with cudaPointerGetAttributes); host
+ * arrays are staged through context-owned device buffers.  The caller owns
+ * every array it passes; the library never keeps a pointer to one after the
+ * call returns.  A context owns all device memory it allocates.
+ *
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
+ * are stream-ordered; only lsg_setup, lsg_pcg_solve, lsg_export and the batch
+ * and server calls synchronise.  A context is not thread-safe: serialise calls
+ * that use the same context.
+ *
+ * Errors: every call returns an lsg_status (0 = OK, < 0 = error); no call
+ * aborts or traps.  Device-side failures (ILU breakdown, an expired wait
+ * budget) are reported through a device error word read back by the
+ * synchronising calls.
+ */
+#ifndef LSG_H
+#define LSG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lsg_ctx lsg_ctx;
+typedef struct lsg_server lsg_server;
+typedef void *lsg_stream_t; /* cudaStream_t */
+
+enum lsg_status {
+    LSG_OK = 0,
+    LSG_ERR_ARG = -1,             /* invalid argument (sizes, null pointer, aliasing) */
+    LSG_ERR_NOMEM = -2,           /* a device or host allocation failed / over budget */
+    LSG_ERR_CUDA = -3,            /* a CUDA runtime error (see lsg_last_error) */
+    LSG_ERR_ILU_BREAKDOWN = -4,   /* ILU(0) pivot U_ii <= 1e-14 |M_ii| (Alg. 2 "assuming they exist") */
+    LSG_ERR_NOT_CONVERGED = -5,   /* k_max reached, or p^T w <= 0 in Algorithm 1 */
+    LSG_ERR_TIMEOUT = -6,         /* a device-side dependency wait exceeded its budget */
+    LSG_ERR_NONFINITE = -7        /* NaN or Inf in the coefficient samples */
+};
+
+enum lsg_precision {
+    LSG_FP64 = 0,        /* every stage in FP64 */
+    LSG_MIXED_TF32 = 1,  /* inner PCG: TF32 tensor-core transforms, FP32 ILU; FP64 refinement */
+    LSG_MIXED_BF16 = 2   /* inner PCG: BF16 tensor-core transforms, FP32 ILU; FP64 refinement */
+};
+
+/* lsg_setup_ex flags */
+#define LSG_SETUP_KEEP_M 1u /* keep an unfactored copy of M for lsg_export(LSG_EXPORT_M) */
+
+/* lsg_export items (host output; sizes from lsg_export_count) */
+enum lsg_export_item {
+    LSG_EXPORT_GAUSS_X = 0,   /* Q nodes, ascending */
+    LSG_EXPORT_GAUSS_W = 1,   /* Q weights */
+    LSG_EXPORT_AHAT = 2,      /* (T+1)^d truncated Legendre coefficients of a, x degree fastest */
+    LSG_EXPORT_BHAT = 3,      /* (T+1)^d truncated Legendre coefficients of b */
+    LSG_EXPORT_BAND_S = 4,    /* (T+1) x (N-1) x (2w+1): S^(t)[i][i+o] = (L_t phi'_i, phi'_{i+o}), o = -w..w */
+    LSG_EXPORT_BAND_M = 5,    /* (T+1) x (N-1) x (2w+1): M^(t)[i][i+o] = (L_t phi_i, phi_{i+o}) */
+    LSG_EXPORT_M = 6,         /* n x S stencil of M (needs LSG_SETUP_KEEP_M) */
+    LSG_EXPORT_LU = 7         /* n x S stencil of the ILU(0) factors (L strictly lower, U upper) */
+};
+
+/* lsg_query items */
+enum lsg_query_item {
+    LSG_Q_UNKNOWNS = 0,     /* n = (N-1)^d */
+    LSG_Q_GRID = 1,         /* Q^d */
+    LSG_Q_HALF_WIDTH = 2,   /* w = T + 2, stencil half-width per direction */
+    LSG_Q_SLOTS = 3,        /* S = (2w+1)^d stencil slots per row, lexicographic (dx fastest) */
+    LSG_Q_LEVELS = 4,       /* wavefront levels of the natural ordering */
+    LSG_Q_DEVICE_BYTES = 5, /* device bytes held by the context */
+    LSG_Q_NNZ = 6,          /* structural nonzeros of M */
+    LSG_Q_PRECISION = 7,
+    LSG_Q_ASSEMBLE_US = 8,  /* setup: M assembly and ordering time, microseconds (CUDA events) */
+    LSG_Q_ILU_US = 9        /* setup: ILU(0) factorisation time, microseconds (CUDA events) */
+};
+
+typedef struct {
+    int iters;            /* PCG loop passes k of Algorithm 1 (summed over refinements in mixed) */
+    int outer_iters;      /* FP64 refinement steps (mixed precision; 0 for FP64) */
+    double relres;        /* recursive sqrt(r^T r)/||F||_2 at exit (innermost) */
+    double relres_true;   /* true ||F - K u||_2 / ||F||_2, computed in FP64 */
+    int status;           /* lsg_status of the solve */
+} lsg_info;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int lsg_version(void);
+/* Static string for a status code. */
+const char *lsg_status_string(int status);
+/* Last CUDA error text recorded by this thread (empty if none). */
+const char *lsg_last_error(void);
+
+/* Instrumentation, no counterpart in the paper: the number of CUDA kernels this
+ * library has launched so far in this process (all contexts, all threads). */
+long long lsg_kernel_launches(void);
+
+/* Legendre-Gauss nodes (roots of L_Q, Sec. 2.2, ascending) and weights,
+ * computed on the device by Newton iteration on the three-term recurrence
+ * (Sec. 2.1).  x, w: host arrays of Q doubles.  Q >= 1. */
+int lsg_gauss(int Q, double *x, double *w);
+
+/* Device bytes lsg_setup_ex would allocate for these sizes (admission model). */
+size_t lsg_footprint_bytes(int d, int N, int T, int Q, int precision);
+
+/* Build a context: Gauss tables, weighted coefficient samples, the truncated
+ * series a_hat, b_hat (Sec. 4.1, the Q-point discrete Legendre transform of the
+ * samples truncated to tensor degree <= T), the band matrices and M
+ * (Sec. 4.2, Kronecker form), and the ILU(0) factors of M in natural order
+ * (Algorithm 2).
+ *   d in {1,2,3}; N >= 3 (N-1 unknowns per direction); T >= 0; Q >= N+1
+ *   (Q <= 0 selects Q = N+2); a, b: Q^d samples (a > 0, b >= 0 expected).
+ * Returns LSG_ERR_NONFINITE for NaN/Inf samples, LSG_ERR_ILU_BREAKDOWN when a
+ * pivot vanishes (the context is still returned so it can be inspected and
+ * destroyed), LSG_ERR_NOMEM when memory is short (no context is returned).
+ * Synchronises `stream`. */
+int lsg_setup(lsg_ctx **out, int d, int N, int T, int Q, const double *a, const double *b,
+              int precision, lsg_stream_t stream);
+int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, const double *b,
+                 int precision, unsigned flags, lsg_stream_t stream);
+
+/* F_k = (f, Psi_k) by Q-point quadrature of the samples f (Q^d, Sec. 3). */
+int lsg_load_vector(lsg_ctx *ctx, const double *f, double *F, lsg_stream_t stream);
+
+/* y = K x = (A + B) x in FP64, matrix-free (Sec. 4.3: Legendre coefficients,
+ * transforms to the Gauss grid, pointwise products with a and b, transposed
+ * transforms).  x, y: n doubles; y must not alias x. */
+int lsg_apply_A(lsg_ctx *ctx, const double *x, double *y, lsg_stream_t stream);
+
+/* z = U^{-1} L^{-1} r: the one-step ILU(0) preconditioner solve (Sec. 4.2,
+ * Algorithms 3 and 4).  r, z: n doubles; z must not alias r.  Mixed-precision
+ * contexts sweep FP32 factors with FP32 accumulation. */
+int lsg_apply_Minv(lsg_ctx *ctx, const double *r, double *z, lsg_stream_t stream);
+
+/* PCG (Algorithm 1) on K u = F with the ILU(0) preconditioner.
+ * u: on entry the initial guess x0, on exit the iterate.  Stops when
+ * sqrt(r^T r) <= rtol ||F||_2 (recursive residual) or after kmax passes.
+ * Mixed-precision contexts run FP64 iterative refinement: r = F - K u in FP64,
+ * an inner PCG in the low precision on r, u += e, until the true FP64
+ * relative residual is <= rtol.  info may be NULL.  Synchronises `stream`. */
+int lsg_pcg_solve(lsg_ctx *ctx, const double *F, double *u, double rtol, int kmax,
+                  lsg_info *info, lsg_stream_t stream);
+
+/* u_N at the Q^d grid (forward transform with the phi tables), for checks. */
+int lsg_eval(lsg_ctx *ctx, const double *u, double *vals, lsg_stream_t stream);
+
+/* Number of doubles lsg_export writes for an item (0 if unavailable). */
+long long lsg_export_count(lsg_ctx *ctx, int item);
+/* Copy an inspection item to the host array `out` (synchronises). */
+int lsg_export(lsg_ctx *ctx, int item, double *out);
+/* Integer properties of a context (-1 for an unknown item). */
+long long lsg_query(lsg_ctx *ctx, int item);
+/* Free a context and all its device memory. */
+int lsg_destroy(lsg_ctx *ctx);
+
+/* Batched PCG over `count` independent contexts (uneven sizes allowed):
+ * the iterations of all problems are interleaved on the device, each problem
+ * stopping at its own tolerance.  F[i], u[i] as in lsg_pcg_solve; infos may
+ * be NULL.  Synchronises `stream`. */
+int lsg_batch_solve(int count, lsg_ctx *const *ctxs, const double *const *F, double *const *u,
+                    double rtol, int kmax, lsg_info *infos, lsg_stream_t stream);
+
+/* ---- serving: continuous batching of solve requests ---------------------- */
+typedef struct {
+    long long id;        /* caller's request id */
+    int d, N, T, Q;      /* problem sizes (Q <= 0: N+2) */
+    int precision;       /* lsg_precision */
+    double rtol;         /* target relative residual */
+    int kmax;
+    const double *a, *b; /* Q^d host samples (copied at submit) */
+    const double *f;     /* Q^d host samples of the right-hand side (copied) */
+} lsg_request;
+
+typedef struct {
+    long long id;
+    lsg_info info;
+    double latency_ms;    /* submit -> solution in host memory */
+    double *u;            /* n doubles, owned by the server until lsg_server_release */
+    long long n;
+} lsg_result;
+
+/* Create a server with an HBM budget (bytes) for admitted requests and up to
+ * max_inflight concurrently running solves (each on its own stream). */
+int lsg_server_create(lsg_server **srv, size_t hbm_budget, int max_inflight);
+/* Queue a request; returns LSG_ERR_NOMEM if it can never fit the budget. */
+int lsg_server_submit(lsg_server *srv, const lsg_request *req);
+/* Collect up to `max` finished results; *count receives how many. */
+int lsg_server_poll(lsg_server *srv, lsg_result *out, int max, int *count);
+/* Block until every queued request has finished. */
+int lsg_server_drain(lsg_server *srv);
+/* Free the solution buffer of a polled result. */
+int lsg_server_release(lsg_server *srv, lsg_result *res);
+int lsg_server_destroy(lsg_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSG_H */

@@ -1,0 +1,527 @@
+// api.cu -- the extern "C" entry points declared in include/lsg.h: argument
+// checks, staging of host arrays, context lifetime, exports.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+
+#include "lsg_internal.cuh"
+
+namespace lsg {
+
+static thread_local char g_last_error[512] = "";
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void record_cuda_error(cudaError_t e, const char *what, const char *file, int line)
+{
+    snprintf(g_last_error, sizeof g_last_error, "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int dalloc(lsg_ctx *c, void **p, size_t bytes, cudaStream_t s)
+{
+    *p = nullptr;
+    if (bytes == 0) return LSG_OK;
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return LSG_ERR_NOMEM;
+    }
+    c->bytes += bytes;
+    return LSG_OK;
+}
+
+int read_dev_error(lsg_ctx *c, cudaStream_t s)
+{
+    int e = 0;
+    LSG_CK(cudaMemcpyAsync(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LSG_CK(cudaStreamSynchronize(s));
+    switch (e) {
+    case DERR_NONE: return LSG_OK;
+    case DERR_BREAKDOWN: return LSG_ERR_ILU_BREAKDOWN;
+    case DERR_TIMEOUT: return LSG_ERR_TIMEOUT;
+    case DERR_NONFINITE: return LSG_ERR_NONFINITE;
+    default: return LSG_ERR_CUDA;
+    }
+}
+
+struct Sizes {
+    size_t tab, tab32, grid, series, band, Lv, Uv, Mkeep, ws, vec, lines;
+};
+
+static Sizes sizes_for(const Geom &g, int precision, unsigned flags)
+{
+    Sizes z{};
+    size_t T1 = g.T + 1, ns = 1;
+    for (int i = 0; i < g.d; ++i) ns *= T1;
+    size_t vsz = precision == LSG_FP64 ? 8 : 4;
+    z.tab = 4 * (size_t)g.QhP * g.KP * 8;
+    z.tab32 = precision == LSG_FP64 ? 0 : 4 * (size_t)g.QhP * g.KP * 4;
+    z.grid = (size_t)g.nq * 8;
+    z.series = ns * 8;
+    z.band = T1 * g.n1 * g.W1 * 8;
+    z.Lv = (size_t)g.n * g.SL * vsz;
+    z.Uv = (size_t)g.n * g.SU * vsz;
+    z.Mkeep = (flags & LSG_SETUP_KEEP_M) ? (size_t)g.n * g.S * 8 : 0;
+    z.ws = workspace_elems(g) * 8;
+    z.vec = (size_t)g.n * 8;
+    z.lines = (size_t)g.nlines * 4;
+    return z;
+}
+
+static size_t footprint(const Geom &g, int precision, unsigned flags)
+{
+    Sizes z = sizes_for(g, precision, flags);
+    size_t b = 2 * (size_t)g.Q * 8 + z.tab + z.tab32 + 3 * z.grid + 2 * z.series + 2 * z.band + z.Lv + z.Uv +
+               z.Mkeep + z.ws + 7 * z.vec + (size_t)g.n * 4 * 2 + 2 * z.lines + 64 + kRedBlocks * 16 +
+               sizeof(PcgState);
+    if (precision != LSG_FP64) b += 5 * (size_t)g.n * 4 + 2 * z.vec + z.ws / 2;
+    // transient setup buffers: sample staging (2 grids) and the precontracted arrays
+    size_t T1 = g.T + 1;
+    size_t nK = g.d == 3 ? T1 * T1 : T1;
+    b += 2 * z.grid + 2 * nK * g.n1 * g.W1 * 8 + (size_t)g.levels * 4;
+    return b;
+}
+
+// Structural nonzeros of M: the pattern is a union of product sets (one per
+// Kronecker term), so count it by inclusion-exclusion over the terms, with the
+// in-grid count of a product set factorising over the axes.
+static long long axis_count(int n1, int T, int kind)  // kind bit0: stiffness band, bit1: mass band
+{
+    long long cnt = 0;
+    for (int o = -(T + 2); o <= T + 2; ++o) {
+        int a = o < 0 ? -o : o;
+        bool in = true;
+        if (kind & 1) in = in && a <= T;
+        if (kind & 2) in = in && a <= T + 2 && (T > 0 || (a % 2) == 0);
+        if (!in) continue;
+        cnt += std::max(0, n1 - a);
+    }
+    return cnt;
+}
+long long structural_nnz(const Geom &g)
+{
+    int nt = g.d + (g.has_b ? 1 : 0);
+    long long total = 0;
+    for (int mask = 1; mask < (1 << nt); ++mask) {
+        long long prod = 1;
+        for (int ax = 0; ax < g.d; ++ax) {
+            int kind = 0;
+            for (int t = 0; t < nt; ++t)
+                if (mask & (1 << t)) kind |= (t == ax) ? 1 : 2;
+            prod *= axis_count(g.n1, g.T, kind);
+        }
+        total += (__builtin_popcount(mask) & 1) ? prod : -prod;
+    }
+    return total;
+}
+
+static int check_sizes(int d, int N, int T, int Q)
+{
+    if (d < 1 || d > 3 || N < 3 || T < 0 || Q < N + 1) return LSG_ERR_ARG;
+    if (N > 8193 || T > 64) return LSG_ERR_ARG;
+    long long n = 1;
+    for (int i = 0; i < d; ++i) n *= (N - 1);
+    if (n > (1ll << 31) - 1) return LSG_ERR_ARG;
+    return LSG_OK;
+}
+
+static void free_ctx(lsg_ctx *c)
+{
+    if (!c) return;
+    void *ptrs[] = {c->gx, c->gw, c->tab, c->tab32, c->Wa, c->Wb, c->Wg, c->ahat, c->bhat, c->bandS, c->bandM,
+                    c->Lv, c->Uv, c->Mkeep, c->order, c->rowflag, c->prog, c->counters, c->err, c->ws, c->ws32,
+                    c->r, c->z, c->p, c->wv, c->xs, c->fs, c->ys, c->red, c->st, c->r32, c->z32, c->p32, c->w32,
+                    c->e32, c->e64, c->u64};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->st_host) cudaFreeHost(c->st_host);
+    delete c;
+}
+
+// Stage an input array: device pointers pass through, host arrays are copied
+// into `stage` (which must hold `count` doubles).
+static int stage_in(const double *p, long long count, double *stage, const double **out, cudaStream_t s)
+{
+    if (is_device_ptr(p)) {
+        *out = p;
+        return LSG_OK;
+    }
+    LSG_CK(cudaMemcpyAsync(stage, p, sizeof(double) * (size_t)count, cudaMemcpyHostToDevice, s));
+    *out = stage;
+    return LSG_OK;
+}
+
+template <typename V>
+__global__ void k_unsplit(long long n, int S, int Sc, int SL, int SU, const V *Lv, const V *Uv, double *out)
+{
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= n * S) return;
+    long long r = idx / S;
+    int s = (int)(idx % S);
+    out[idx] = s < Sc ? (double)Lv[r * SL + s] : (double)Uv[r * SU + (s - Sc)];
+}
+
+}  // namespace lsg
+
+using namespace lsg;
+
+extern "C" {
+
+int lsg_version(void) { return 100; }
+
+const char *lsg_status_string(int st)
+{
+    switch (st) {
+    case LSG_OK: return "ok";
+    case LSG_ERR_ARG: return "invalid argument";
+    case LSG_ERR_NOMEM: return "out of memory";
+    case LSG_ERR_CUDA: return "CUDA error";
+    case LSG_ERR_ILU_BREAKDOWN: return "ILU(0) breakdown (non-positive pivot)";
+    case LSG_ERR_NOT_CONVERGED: return "PCG did not converge";
+    case LSG_ERR_TIMEOUT: return "device wait budget expired";
+    case LSG_ERR_NONFINITE: return "non-finite coefficient samples";
+    default: return "unknown status";
+    }
+}
+
+const char *lsg_last_error(void) { return g_last_error; }
+
+long long lsg_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int lsg_gauss(int Q, double *x, double *w)
+{
+    if (Q < 1 || !x || !w) return LSG_ERR_ARG;
+    double *dx = nullptr, *dw = nullptr;
+    LSG_CK(cudaMalloc((void **)&dx, sizeof(double) * Q));
+    if (cudaMalloc((void **)&dw, sizeof(double) * Q) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dx);
+        return LSG_ERR_NOMEM;
+    }
+    int st = gauss_rule(Q, dx, dw, 0);
+    if (st == LSG_OK) {
+        cudaError_t e1 = cudaMemcpy(x, dx, sizeof(double) * Q, cudaMemcpyDeviceToHost);
+        cudaError_t e2 = cudaMemcpy(w, dw, sizeof(double) * Q, cudaMemcpyDeviceToHost);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) st = LSG_ERR_CUDA;
+    }
+    cudaFree(dx);
+    cudaFree(dw);
+    return st;
+}
+
+size_t lsg_footprint_bytes(int d, int N, int T, int Q, int precision)
+{
+    if (Q <= 0) Q = N + 2;
+    if (check_sizes(d, N, T, Q) != LSG_OK) return 0;
+    return footprint(make_geom(d, N, T, Q), precision, 0);
+}
+
+int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, const double *b, int precision,
+                 unsigned flags, lsg_stream_t stream)
+{
+    if (!out || !a || !b) return LSG_ERR_ARG;
+    *out = nullptr;
+    if (Q <= 0) Q = N + 2;
+    LSG_TRY(check_sizes(d, N, T, Q));
+    if (precision < LSG_FP64 || precision > LSG_MIXED_BF16) return LSG_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    lsg_ctx *c = new lsg_ctx{};
+    c->g = make_geom(d, N, T, Q);
+    c->precision = precision;
+    c->flags = flags;
+    LSG_CK(cudaGetDevice(&c->device));
+    {
+        // keep freed context memory in the stream-ordered pool for the next setup
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
+            unsigned long long thr = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        cudaGetLastError();
+    }
+    const Geom &g = c->g;
+    Sizes z = sizes_for(g, precision, flags);
+    int st = LSG_OK;
+#define ALLOC(ptr, bytes)                                                      \
+    do {                                                                       \
+        if (st == LSG_OK) st = dalloc(c, (void **)&(ptr), (bytes), s);         \
+    } while (0)
+    ALLOC(c->gx, sizeof(double) * Q);
+    ALLOC(c->gw, sizeof(double) * Q);
+    ALLOC(c->tab, z.tab);
+    if (z.tab32) ALLOC(c->tab32, z.tab32);
+    ALLOC(c->Wa, z.grid);
+    ALLOC(c->Wb, z.grid);
+    ALLOC(c->Wg, z.grid);
+    ALLOC(c->ahat, z.series);
+    ALLOC(c->bhat, z.series);
+    ALLOC(c->bandS, z.band);
+    ALLOC(c->bandM, z.band);
+    ALLOC(c->Lv, z.Lv);
+    ALLOC(c->Uv, z.Uv);
+    if (z.Mkeep) ALLOC(c->Mkeep, z.Mkeep);
+    ALLOC(c->order, sizeof(int) * (size_t)g.n);
+    ALLOC(c->rowflag, sizeof(unsigned) * (size_t)g.n);
+    ALLOC(c->prog, 2 * z.lines);
+    ALLOC(c->counters, sizeof(unsigned) * 16);
+    ALLOC(c->err, sizeof(int) * 4);
+    ALLOC(c->ws, z.ws);
+    ALLOC(c->r, z.vec);
+    ALLOC(c->z, z.vec);
+    ALLOC(c->p, z.vec);
+    ALLOC(c->wv, z.vec);
+    ALLOC(c->xs, z.vec);
+    ALLOC(c->fs, std::max(z.vec, z.grid));
+    ALLOC(c->ys, z.vec);
+    ALLOC(c->red, sizeof(double) * 2 * kRedBlocks);
+    ALLOC(c->st, sizeof(PcgState));
+    if (precision != LSG_FP64) {
+        ALLOC(c->r32, (size_t)g.n * 4);
+        ALLOC(c->z32, (size_t)g.n * 4);
+        ALLOC(c->p32, (size_t)g.n * 4);
+        ALLOC(c->w32, (size_t)g.n * 4);
+        ALLOC(c->e32, (size_t)g.n * 4);
+        ALLOC(c->e64, z.vec);
+        ALLOC(c->u64, z.vec);
+        ALLOC(c->ws32, z.ws / 2);
+    }
+    double *sa = nullptr, *sb = nullptr;
+    bool ha = !is_device_ptr(a), hb = !is_device_ptr(b);
+    if (ha) ALLOC(sa, z.grid);
+    if (hb) ALLOC(sb, z.grid);
+#undef ALLOC
+    if (st == LSG_OK && cudaMallocHost((void **)&c->st_host, sizeof(PcgState)) != cudaSuccess) {
+        cudaGetLastError();
+        st = LSG_ERR_NOMEM;
+    }
+    if (st != LSG_OK) {
+        if (sa) cudaFreeAsync(sa, s);
+        if (sb) cudaFreeAsync(sb, s);
+        cudaStreamSynchronize(s);
+        free_ctx(c);
+        return st;
+    }
+    c->bytes += 0;
+    const double *da = a, *db = b;
+    auto fail = [&](int code) {
+        if (sa) cudaFreeAsync(sa, s);
+        if (sb) cudaFreeAsync(sb, s);
+        cudaStreamSynchronize(s);
+        free_ctx(c);
+        return code;
+    };
+    if (ha) {
+        if (cudaMemcpyAsync(sa, a, z.grid, cudaMemcpyHostToDevice, s) != cudaSuccess) return fail(LSG_ERR_CUDA);
+        da = sa;
+    }
+    if (hb) {
+        if (cudaMemcpyAsync(sb, b, z.grid, cudaMemcpyHostToDevice, s) != cudaSuccess) return fail(LSG_ERR_CUDA);
+        db = sb;
+    }
+    if (cudaMemsetAsync(c->err, 0, sizeof(int) * 4, s) != cudaSuccess) return fail(LSG_ERR_CUDA);
+    st = build_tables(c, da, db, s);
+    if (st != LSG_OK) return fail(st);
+    int derr = read_dev_error(c, s);
+    if (derr != LSG_OK) return fail(derr);
+    st = build_preconditioner(c, s);
+    if (st != LSG_OK) return fail(st);
+    if (sa) cudaFreeAsync(sa, s);
+    if (sb) cudaFreeAsync(sb, s);
+    sa = sb = nullptr;
+    derr = read_dev_error(c, s);
+    if (derr == LSG_ERR_TIMEOUT || derr == LSG_ERR_CUDA) return fail(derr);
+    *out = c;
+    return derr;  // LSG_OK or LSG_ERR_ILU_BREAKDOWN (context kept for inspection)
+}
+
+int lsg_setup(lsg_ctx **out, int d, int N, int T, int Q, const double *a, const double *b, int precision,
+              lsg_stream_t stream)
+{
+    return lsg_setup_ex(out, d, N, T, Q, a, b, precision, 0u, stream);
+}
+
+int lsg_destroy(lsg_ctx *c)
+{
+    if (!c) return LSG_ERR_ARG;
+    cudaDeviceSynchronize();
+    free_ctx(c);
+    return LSG_OK;
+}
+
+int lsg_load_vector(lsg_ctx *c, const double *f, double *F, lsg_stream_t stream)
+{
+    if (!c || !f || !F) return LSG_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double *df;
+    LSG_TRY(stage_in(f, c->g.nq, c->fs, &df, s));
+    bool hF = !is_device_ptr(F);
+    double *dF = hF ? c->ys : F;
+    LSG_TRY(load_vector(c, df, dF, s));
+    if (hF) {
+        LSG_CK(cudaMemcpyAsync(F, dF, sizeof(double) * (size_t)c->g.n, cudaMemcpyDeviceToHost, s));
+        LSG_CK(cudaStreamSynchronize(s));
+    }
+    return LSG_OK;
+}
+
+int lsg_apply_A(lsg_ctx *c, const double *x, double *y, lsg_stream_t stream)
+{
+    if (!c || !x || !y || x == y) return LSG_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double *dx;
+    LSG_TRY(stage_in(x, c->g.n, c->xs, &dx, s));
+    bool hy = !is_device_ptr(y);
+    double *dy = hy ? c->ys : y;
+    LSG_TRY(apply_K(c, dx, dy, nullptr, s));
+    if (hy) {
+        LSG_CK(cudaMemcpyAsync(y, dy, sizeof(double) * (size_t)c->g.n, cudaMemcpyDeviceToHost, s));
+        LSG_CK(cudaStreamSynchronize(s));
+    }
+    return LSG_OK;
+}
+
+int lsg_apply_Minv(lsg_ctx *c, const double *r, double *z, lsg_stream_t stream)
+{
+    if (!c || !r || !z || r == z) return LSG_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double *dr;
+    LSG_TRY(stage_in(r, c->g.n, c->xs, &dr, s));
+    bool hz = !is_device_ptr(z);
+    double *dz = hz ? c->wv : z;
+    LSG_TRY(apply_Minv(c, dr, dz, nullptr, s));
+    if (hz) {
+        LSG_CK(cudaMemcpyAsync(z, dz, sizeof(double) * (size_t)c->g.n, cudaMemcpyDeviceToHost, s));
+        LSG_CK(cudaStreamSynchronize(s));
+        return read_dev_error(c, s);
+    }
+    return LSG_OK;
+}
+
+int lsg_pcg_solve(lsg_ctx *c, const double *F, double *u, double rtol, int kmax, lsg_info *info,
+                  lsg_stream_t stream)
+{
+    if (!c || !F || !u || !(rtol >= 0.0) || kmax < 0) return LSG_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double *dF;
+    LSG_TRY(stage_in(F, c->g.n, c->fs, &dF, s));
+    bool hu = !is_device_ptr(u);
+    double *du = u;
+    if (hu) {
+        du = c->xs;
+        LSG_CK(cudaMemcpyAsync(du, u, sizeof(double) * (size_t)c->g.n, cudaMemcpyHostToDevice, s));
+    }
+    int st = pcg_fp64(c, dF, du, rtol, kmax, info, s);
+    if (hu) {
+        LSG_CK(cudaMemcpyAsync(u, du, sizeof(double) * (size_t)c->g.n, cudaMemcpyDeviceToHost, s));
+        LSG_CK(cudaStreamSynchronize(s));
+    }
+    return st;
+}
+
+int lsg_eval(lsg_ctx *c, const double *u, double *vals, lsg_stream_t stream)
+{
+    if (!c || !u || !vals) return LSG_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double *du;
+    LSG_TRY(stage_in(u, c->g.n, c->xs, &du, s));
+    bool hv = !is_device_ptr(vals);
+    double *dv = hv ? c->fs : vals;
+    LSG_TRY(eval_grid(c, du, dv, s));
+    if (hv) {
+        LSG_CK(cudaMemcpyAsync(vals, dv, sizeof(double) * (size_t)c->g.nq, cudaMemcpyDeviceToHost, s));
+        LSG_CK(cudaStreamSynchronize(s));
+    }
+    return LSG_OK;
+}
+
+long long lsg_export_count(lsg_ctx *c, int item)
+{
+    if (!c) return 0;
+    const Geom &g = c->g;
+    long long ns = 1;
+    for (int i = 0; i < g.d; ++i) ns *= (g.T + 1);
+    switch (item) {
+    case LSG_EXPORT_GAUSS_X:
+    case LSG_EXPORT_GAUSS_W: return g.Q;
+    case LSG_EXPORT_AHAT:
+    case LSG_EXPORT_BHAT: return ns;
+    case LSG_EXPORT_BAND_S:
+    case LSG_EXPORT_BAND_M: return (long long)(g.T + 1) * g.n1 * g.W1;
+    case LSG_EXPORT_M: return c->Mkeep ? g.n * g.S : 0;
+    case LSG_EXPORT_LU: return g.n * g.S;
+    default: return 0;
+    }
+}
+
+int lsg_export(lsg_ctx *c, int item, double *out)
+{
+    if (!c || !out) return LSG_ERR_ARG;
+    long long cnt = lsg_export_count(c, item);
+    if (cnt <= 0) return LSG_ERR_ARG;
+    const double *src = nullptr;
+    switch (item) {
+    case LSG_EXPORT_GAUSS_X: src = c->gx; break;
+    case LSG_EXPORT_GAUSS_W: src = c->gw; break;
+    case LSG_EXPORT_AHAT: src = c->ahat; break;
+    case LSG_EXPORT_BHAT: src = c->bhat; break;
+    case LSG_EXPORT_BAND_S: src = c->bandS; break;
+    case LSG_EXPORT_BAND_M: src = c->bandM; break;
+    case LSG_EXPORT_M: src = c->Mkeep; break;
+    default: break;
+    }
+    LSG_CK(cudaDeviceSynchronize());
+    if (item == LSG_EXPORT_LU) {
+        double *tmp = nullptr;
+        LSG_CK(cudaMalloc((void **)&tmp, sizeof(double) * (size_t)cnt));
+        const Geom &g = c->g;
+        unsigned blocks = (unsigned)((cnt + 255) / 256);
+        if (c->precision == LSG_FP64)
+            k_unsplit<double><<<blocks, 256>>>(g.n, g.S, g.Sc, g.SL, g.SU, (const double *)c->Lv, (const double *)c->Uv, tmp);
+        else
+            k_unsplit<float><<<blocks, 256>>>(g.n, g.S, g.Sc, g.SL, g.SU, (const float *)c->Lv, (const float *)c->Uv, tmp);
+        cudaError_t e = cudaMemcpy(out, tmp, sizeof(double) * (size_t)cnt, cudaMemcpyDeviceToHost);
+        cudaFree(tmp);
+        LSG_CK(e);
+        return LSG_OK;
+    }
+    LSG_CK(cudaMemcpy(out, src, sizeof(double) * (size_t)cnt, cudaMemcpyDeviceToHost));
+    return LSG_OK;
+}
+
+long long lsg_query(lsg_ctx *c, int item)
+{
+    if (!c) return -1;
+    const Geom &g = c->g;
+    switch (item) {
+    case LSG_Q_UNKNOWNS: return g.n;
+    case LSG_Q_GRID: return g.nq;
+    case LSG_Q_HALF_WIDTH: return g.w;
+    case LSG_Q_SLOTS: return g.S;
+    case LSG_Q_LEVELS: return g.levels;
+    case LSG_Q_DEVICE_BYTES: return (long long)c->bytes;
+    case LSG_Q_NNZ: return structural_nnz(g);
+    case LSG_Q_PRECISION: return c->precision;
+    case LSG_Q_ASSEMBLE_US: return (long long)(c->t_assemble_ms * 1000.0f);
+    case LSG_Q_ILU_US: return (long long)(c->t_ilu_ms * 1000.0f);
+    default: return -1;
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,88 @@
+// batch.cu -- batched PCG over many independent problems (uneven sizes).
+// Every problem runs Algorithm 1 on its own stream; the host advances all runs
+// without blocking on any one of them, so the kernels of different problems
+// overlap on the device and each problem stops at its own tolerance.
+#include <thread>
+#include <vector>
+
+#include "lsg_internal.cuh"
+
+using namespace lsg;
+
+extern "C" int lsg_batch_solve(int count, lsg_ctx *const *ctxs, const double *const *F, double *const *u,
+                               double rtol, int kmax, lsg_info *infos, lsg_stream_t stream)
+{
+    if (count < 0 || (count > 0 && (!ctxs || !F || !u)) || !(rtol >= 0.0) || kmax < 0) return LSG_ERR_ARG;
+    if (count == 0) return LSG_OK;
+    for (int i = 0; i < count; ++i)
+        if (!ctxs[i] || !F[i] || !u[i]) return LSG_ERR_ARG;
+    cudaStream_t s0 = (cudaStream_t)stream;
+    std::vector<cudaStream_t> st(count, nullptr);
+    std::vector<PcgRun> runs(count);
+    std::vector<bool> fin(count, false), hostu(count, false);
+    std::vector<const double *> dF(count);
+    std::vector<double *> du(count);
+    cudaEvent_t fork;
+    LSG_CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    LSG_CK(cudaEventRecord(fork, s0));
+    int status = LSG_OK;
+    for (int i = 0; i < count; ++i) {
+        runs[i] = PcgRun{};
+        LSG_CK(cudaStreamCreateWithFlags(&st[i], cudaStreamNonBlocking));
+        LSG_CK(cudaStreamWaitEvent(st[i], fork, 0));
+        lsg_ctx *c = ctxs[i];
+        const long long n = c->g.n;
+        if (is_device_ptr(F[i])) {
+            dF[i] = F[i];
+        } else {
+            LSG_CK(cudaMemcpyAsync(c->fs, F[i], sizeof(double) * n, cudaMemcpyHostToDevice, st[i]));
+            dF[i] = c->fs;
+        }
+        hostu[i] = !is_device_ptr(u[i]);
+        du[i] = u[i];
+        if (hostu[i]) {
+            du[i] = c->xs;
+            LSG_CK(cudaMemcpyAsync(du[i], u[i], sizeof(double) * n, cudaMemcpyHostToDevice, st[i]));
+        }
+        int s = pcg_start(runs[i], c, dF[i], du[i], rtol, kmax, st[i]);
+        if (s != LSG_OK) {
+            fin[i] = true;
+            runs[i].status = s;
+            if (status == LSG_OK) status = s;
+        }
+    }
+    int left = 0;
+    for (int i = 0; i < count; ++i) left += fin[i] ? 0 : 1;
+    while (left > 0) {
+        bool progressed = false;
+        for (int i = 0; i < count; ++i) {
+            if (fin[i]) continue;
+            int ph = runs[i].phase, la = runs[i].launched;
+            bool f = false;
+            int s = pcg_poll(runs[i], st[i], false, &f);
+            if (f || s != LSG_OK) {
+                fin[i] = true;
+                --left;
+                if (s != LSG_OK && status == LSG_OK) status = s;
+            }
+            if (f || runs[i].phase != ph || runs[i].launched != la) progressed = true;
+        }
+        if (!progressed) std::this_thread::yield();
+    }
+    for (int i = 0; i < count; ++i) {
+        lsg_ctx *c = ctxs[i];
+        if (hostu[i])
+            LSG_CK(cudaMemcpyAsync(u[i], du[i], sizeof(double) * c->g.n, cudaMemcpyDeviceToHost, st[i]));
+        cudaEvent_t j;
+        LSG_CK(cudaEventCreateWithFlags(&j, cudaEventDisableTiming));
+        LSG_CK(cudaEventRecord(j, st[i]));
+        LSG_CK(cudaStreamWaitEvent(s0, j, 0));
+        LSG_CK(cudaStreamSynchronize(st[i]));
+        cudaEventDestroy(j);
+        if (infos) pcg_info(runs[i], &infos[i]);
+        pcg_release(runs[i]);
+        cudaStreamDestroy(st[i]);
+    }
+    cudaEventDestroy(fork);
+    return status;
+}

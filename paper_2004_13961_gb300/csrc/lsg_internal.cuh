@@ -1,0 +1,175 @@
+// lsg_internal.cuh -- context layout, geometry and small device helpers shared by
+// the CUDA sources of the solver library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lsg.h"
+
+namespace lsg {
+
+// ---------------------------------------------------------------------------
+// error handling
+void record_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+#define LSG_CK(call)                                                          \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) {                                              \
+            ::lsg::record_cuda_error(e_, #call, __FILE__, __LINE__);          \
+            return LSG_ERR_CUDA;                                              \
+        }                                                                     \
+    } while (0)
+
+#define LSG_TRY(expr)                                                         \
+    do {                                                                      \
+        int s_ = (expr);                                                      \
+        if (s_ != LSG_OK) return s_;                                          \
+    } while (0)
+
+// device error word values (first error wins)
+enum DevErr : int { DERR_NONE = 0, DERR_BREAKDOWN = 1, DERR_TIMEOUT = 2, DERR_NONFINITE = 3 };
+
+// wait budget of every device-side spin, in SM clock cycles (clock64 is local to
+// the SM and cheap to read; ~4 s at 2 GHz)
+constexpr long long kSpinBudgetCycles = 8000000000ll;
+
+// ---------------------------------------------------------------------------
+// geometry of one problem
+struct Geom {
+    int d, N, n1, Q, Qh, T, w, W1;
+    int S, Sc;            // stencil slots (2w+1)^d and the centre slot
+    int SL, SU;           // padded row lengths of the strictly-lower / diag+upper stencil halves
+    int ne, no;           // even / odd basis counts ceil(n1/2), floor(n1/2)
+    int KP, QhP;          // padded table dims (columns: half basis count, rows: half node count)
+    long long n, nq;      // unknowns n1^d, grid points Q^d
+    long long nlines;     // n1^(d-1)
+    int levels;           // wavefront levels (n1-1) * sum_{a<d} (w+1)^a + 1
+    int has_b;            // reaction term present (pattern includes the mass term)
+};
+
+Geom make_geom(int d, int N, int T, int Q);
+
+// pinned + device scalars of one PCG run (device-resident Algorithm 1 state)
+struct PcgState {
+    double rho, rho_old, alpha, beta, pw, rr, nF2, eps2, tr;  // tr: true residual^2 scratch
+    int k, kmax, done, status;
+    int pad[4];
+};
+
+// reduction scratch: fixed grid so that sums are deterministic
+constexpr int kRedBlocks = 296;   // 2 x 148..152 SMs, fixed for determinism
+constexpr int kRedThreads = 256;
+
+}  // namespace lsg
+
+struct lsg_ctx {
+    lsg::Geom g;
+    int precision;
+    int device;
+    unsigned flags;
+    size_t bytes;
+
+    // Gauss rule and folded transform tables (FP64)
+    double *gx, *gw;           // Q nodes / weights
+    double *tab;               // 4 blocks of QhP*KP: phiE, phiO, dphiE, dphiO
+    float *tab32;              // FP32 copies (mixed)
+    double *Wa, *Wb, *Wg;      // w(x)w(y)w(z) * a, * b, and the weights alone (Q^d)
+    double *ahat, *bhat;       // (T+1)^d
+    double *bandS, *bandM;     // (T+1) x n1 x W1
+
+    // ILU(0) factors in split stencil storage: Lv [n][SL] strictly lower slots,
+    // Uv [n][SU] diagonal then strictly upper slots (double, or float when mixed)
+    void *Lv, *Uv;
+    double *Mkeep;             // optional copy of M ([n][S])
+    int *order;                // rows in wavefront-level order
+    unsigned *rowflag;         // ILU row completion flags
+    unsigned *prog;            // sweep progress per line (2 x nlines: forward, backward)
+    unsigned *counters;        // claim counters (ILU, sweep L, sweep U, reductions)
+    int *err;                  // device error word
+
+    // matrix-free product workspace
+    double *ws;
+    size_t ws_elems;
+    float *ws32;
+
+    // PCG vectors and reductions
+    double *r, *z, *p, *wv, *xs, *fs, *ys;   // xs/fs/ys: staging for host arguments
+    double *red;               // kRedBlocks partials
+    lsg::PcgState *st;         // device state
+    lsg::PcgState *st_host;    // pinned mirror
+    // mixed precision inner vectors
+    float *r32, *z32, *p32, *w32, *e32;
+    double *e64, *u64;
+
+    // setup stage times (milliseconds, CUDA events): tables, assembly, ILU(0)
+    float t_tables_ms, t_assemble_ms, t_ilu_ms;
+};
+
+namespace lsg {
+
+// allocation helpers (device memory accounted in ctx->bytes)
+int dalloc(lsg_ctx *c, void **p, size_t bytes, cudaStream_t s);
+bool is_device_ptr(const void *p);
+
+// kernels / drivers implemented in the .cu files
+int build_tables(lsg_ctx *c, const double *a_dev, const double *b_dev, cudaStream_t s);
+int build_preconditioner(lsg_ctx *c, cudaStream_t s);
+int apply_K(lsg_ctx *c, const double *x, double *y, const int *done, cudaStream_t s);
+int load_vector(lsg_ctx *c, const double *f, double *F, cudaStream_t s);
+int eval_grid(lsg_ctx *c, const double *u, double *vals, cudaStream_t s);
+int apply_Minv(lsg_ctx *c, const double *r, double *z, const int *done, cudaStream_t s);
+int pcg_fp64(lsg_ctx *c, const double *F, double *u, double rtol, int kmax, lsg_info *info,
+             cudaStream_t s);
+
+// non-blocking PCG run (Algorithm 1) used by the batched and serving forms
+struct PcgRun {
+    lsg_ctx *c;
+    const double *F;
+    double *x;
+    int kmax, launched, chunk, phase, status;
+    cudaEvent_t ev;
+};
+int pcg_start(PcgRun &R, lsg_ctx *c, const double *F, double *x, double rtol, int kmax, cudaStream_t s);
+int pcg_poll(PcgRun &R, cudaStream_t s, bool wait, bool *finished);
+void pcg_info(const PcgRun &R, lsg_info *info);
+void pcg_release(PcgRun &R);
+int read_dev_error(lsg_ctx *c, cudaStream_t s);
+int check_finite(lsg_ctx *c, const double *v, long long n, cudaStream_t s);
+size_t workspace_elems(const Geom &g);
+int gauss_rule(int Q, double *x, double *w, cudaStream_t s);
+long long structural_nnz(const Geom &g);
+
+// host-side count of kernel launches issued by the library (all contexts)
+void count_launch();
+
+// ---------------------------------------------------------------------------
+// device helpers
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void set_err(int *err, int code) { atomicCAS(err, 0, code); }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace lsg

@@ -1,0 +1,338 @@
+// pcg.cu -- Algorithm 1 (PCG) kept on the device.  Each iteration is a fixed
+// sequence of kernels on one stream: z = M^-1 r (two sweeps), rho = r^T z and
+// beta, p = z + beta p, w = K p (transforms), alpha = rho / p^T w, then
+// x += alpha p, r -= alpha w and r^T r.  Every reduction uses a fixed grid and
+// a last-block combine in block order, so results are bitwise reproducible.
+// The stop test of Algorithm 1 is evaluated on the device and written to a
+// `done` word; every kernel of later iterations returns at once when it is
+// set, so the host only polls the state every few iterations.
+#include <math.h>
+
+#include <algorithm>
+
+#include "lsg_internal.cuh"
+
+namespace lsg {
+
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (wid == 0) {
+        t = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+        t = warp_sum(t);
+    }
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+// Returns true in every thread of the block that finishes last; that block
+// then combines the partials (in block order) and resets the counter.
+__device__ __forceinline__ bool last_block(unsigned *cnt)
+{
+    __shared__ bool am_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = (atomicAdd(cnt, 1u) == gridDim.x - 1);
+    __syncthreads();
+    return am_last;
+}
+
+__device__ __forceinline__ double combine(const double *red, int stride, int which, double *sh)
+{
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(red + (size_t)b * stride + which);
+    // fixed combine order: thread-strided partials then the block tree
+    return block_sum(v, sh);
+}
+
+// r = F - Kx; nF2 = F.F; rr = r.r; initial stop test.
+__global__ void __launch_bounds__(kRedThreads) k_init(long long n, const double *F, const double *Kx, double *r,
+                                                     double *red, unsigned *cnt, PcgState *st)
+{
+    __shared__ double sh[32];
+    double a = 0.0, b = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double f = F[i], ri = f - Kx[i];
+        r[i] = ri;
+        a += f * f;
+        b += ri * ri;
+    }
+    a = block_sum(a, sh);
+    b = block_sum(b, sh);
+    if (threadIdx.x == 0) {
+        red[2 * blockIdx.x] = a;
+        red[2 * blockIdx.x + 1] = b;
+    }
+    if (last_block(cnt)) {
+        double nF2 = combine(red, 2, 0, sh);
+        double rr = combine(red, 2, 1, sh);
+        if (threadIdx.x == 0) {
+            st->nF2 = nF2;
+            st->rr = rr;
+            st->k = 0;
+            st->rho = 0.0;
+            st->done = (rr <= st->eps2 * nF2 || st->kmax <= 0) ? 1 : 0;
+            *cnt = 0;
+        }
+    }
+}
+
+// rho = r.z ; beta = rho / rho_old (first pass: beta = 0)
+__global__ void __launch_bounds__(kRedThreads) k_rz(long long n, const double *r, const double *z, double *red,
+                                                   unsigned *cnt, PcgState *st)
+{
+    if (st->done) return;
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a += r[i] * z[i];
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) red[blockIdx.x] = a;
+    if (last_block(cnt)) {
+        double rho = combine(red, 1, 0, sh);
+        if (threadIdx.x == 0) {
+            st->beta = (st->k == 0) ? 0.0 : rho / st->rho;
+            st->rho_old = st->rho;
+            st->rho = rho;
+            *cnt = 0;
+        }
+    }
+}
+
+// p = z + beta p   (p = z on the first pass)
+__global__ void k_pupd(long long n, const double *z, double *p, const PcgState *st)
+{
+    if (st->done) return;
+    const double beta = st->beta;
+    const bool first = st->k == 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = first ? z[i] : z[i] + beta * p[i];
+}
+
+// pw = p.w ; alpha = rho / pw  (pw <= 0: stop, not converged)
+__global__ void __launch_bounds__(kRedThreads) k_pw(long long n, const double *p, const double *w, double *red,
+                                                   unsigned *cnt, PcgState *st)
+{
+    if (st->done) return;
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a += p[i] * w[i];
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) red[blockIdx.x] = a;
+    if (last_block(cnt)) {
+        double pw = combine(red, 1, 0, sh);
+        if (threadIdx.x == 0) {
+            st->pw = pw;
+            if (!(pw > 0.0)) {
+                st->status = LSG_ERR_NOT_CONVERGED;
+                st->done = 1;
+            } else {
+                st->alpha = st->rho / pw;
+            }
+            *cnt = 0;
+        }
+    }
+}
+
+// x += alpha p ; r -= alpha w ; rr = r.r ; k += 1 ; stop test of Algorithm 1
+__global__ void __launch_bounds__(kRedThreads) k_xr(long long n, double *x, double *r, const double *p,
+                                                   const double *w, double *red, unsigned *cnt, PcgState *st)
+{
+    if (st->done) return;
+    __shared__ double sh[32];
+    const double alpha = st->alpha;
+    double a = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        x[i] += alpha * p[i];
+        double ri = r[i] - alpha * w[i];
+        r[i] = ri;
+        a += ri * ri;
+    }
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) red[blockIdx.x] = a;
+    if (last_block(cnt)) {
+        double rr = combine(red, 1, 0, sh);
+        if (threadIdx.x == 0) {
+            st->rr = rr;
+            st->k += 1;
+            if (rr <= st->eps2 * st->nF2 || st->k >= st->kmax) st->done = 1;
+            *cnt = 0;
+        }
+    }
+}
+
+// tr = |F - Kx|^2 (true residual), nF2 refreshed
+__global__ void __launch_bounds__(kRedThreads) k_true(long long n, const double *F, const double *Kx, double *red,
+                                                     unsigned *cnt, PcgState *st)
+{
+    __shared__ double sh[32];
+    double a = 0.0, b = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double f = F[i], d = f - Kx[i];
+        a += d * d;
+        b += f * f;
+    }
+    a = block_sum(a, sh);
+    b = block_sum(b, sh);
+    if (threadIdx.x == 0) {
+        red[2 * blockIdx.x] = a;
+        red[2 * blockIdx.x + 1] = b;
+    }
+    if (last_block(cnt)) {
+        double tr = combine(red, 2, 0, sh);
+        double nf = combine(red, 2, 1, sh);
+        if (threadIdx.x == 0) {
+            st->tr = tr;
+            st->nF2 = nf;
+            *cnt = 0;
+        }
+    }
+}
+
+static int iteration(lsg_ctx *c, double *x, cudaStream_t s)
+{
+    const long long n = c->g.n;
+    const int *done = &c->st->done;
+    unsigned *cnt = c->counters + 4;
+    LSG_TRY(apply_Minv(c, c->r, c->z, done, s));
+    ::lsg::count_launch();
+    k_rz<<<kRedBlocks, kRedThreads, 0, s>>>(n, c->r, c->z, c->red, cnt, c->st);
+    ::lsg::count_launch();
+    k_pupd<<<kRedBlocks, kRedThreads, 0, s>>>(n, c->z, c->p, c->st);
+    LSG_TRY(apply_K(c, c->p, c->wv, done, s));
+    ::lsg::count_launch();
+    k_pw<<<kRedBlocks, kRedThreads, 0, s>>>(n, c->p, c->wv, c->red, cnt, c->st);
+    ::lsg::count_launch();
+    k_xr<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, c->r, c->p, c->wv, c->red, cnt, c->st);
+    LSG_CK(cudaGetLastError());
+    return LSG_OK;
+}
+
+// Copy the device state (and the device error word) to the pinned mirror and
+// mark the point with the run's event.
+static int snapshot(PcgRun &R, cudaStream_t s)
+{
+    lsg_ctx *c = R.c;
+    LSG_CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    LSG_CK(cudaMemcpyAsync(&c->st_host->pad[0], c->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LSG_CK(cudaEventRecord(R.ev, s));
+    return LSG_OK;
+}
+
+int pcg_start(PcgRun &R, lsg_ctx *c, const double *F, double *x, double rtol, int kmax, cudaStream_t s)
+{
+    R.c = c;
+    R.F = F;
+    R.x = x;
+    R.kmax = kmax;
+    R.launched = 0;
+    R.chunk = 2;
+    R.phase = 0;
+    R.status = LSG_OK;
+    if (!R.ev) LSG_CK(cudaEventCreateWithFlags(&R.ev, cudaEventDisableTiming));
+    const long long n = c->g.n;
+    PcgState *h = c->st_host;
+    *h = PcgState{};
+    h->eps2 = rtol * rtol;
+    h->kmax = kmax;
+    LSG_CK(cudaMemcpyAsync(c->st, h, sizeof(PcgState), cudaMemcpyHostToDevice, s));
+    LSG_CK(cudaMemsetAsync(c->counters + 4, 0, sizeof(unsigned), s));
+    LSG_TRY(apply_K(c, x, c->wv, nullptr, s));
+    ::lsg::count_launch();
+    k_init<<<kRedBlocks, kRedThreads, 0, s>>>(n, F, c->wv, c->r, c->red, c->counters + 4, c->st);
+    LSG_CK(cudaGetLastError());
+    return snapshot(R, s);
+}
+
+static int dev_err_status(int e)
+{
+    switch (e) {
+    case DERR_NONE: return LSG_OK;
+    case DERR_BREAKDOWN: return LSG_ERR_ILU_BREAKDOWN;
+    case DERR_TIMEOUT: return LSG_ERR_TIMEOUT;
+    case DERR_NONFINITE: return LSG_ERR_NONFINITE;
+    default: return LSG_ERR_CUDA;
+    }
+}
+
+// Advance a run by one step if its last snapshot has landed.  Non-blocking
+// unless `wait` is set.  *finished becomes true once the run is complete.
+int pcg_poll(PcgRun &R, cudaStream_t s, bool wait, bool *finished)
+{
+    *finished = false;
+    if (R.phase == 2) {
+        *finished = true;
+        return R.status;
+    }
+    if (wait) {
+        LSG_CK(cudaEventSynchronize(R.ev));
+    } else {
+        cudaError_t q = cudaEventQuery(R.ev);
+        if (q == cudaErrorNotReady) return LSG_OK;
+        LSG_CK(q);
+    }
+    lsg_ctx *c = R.c;
+    PcgState *h = c->st_host;
+    int derr = dev_err_status(h->pad[0]);
+    if (R.phase == 1 || derr == LSG_ERR_TIMEOUT) {
+        R.status = h->status;
+        if (R.status == LSG_OK && !(h->rr <= h->eps2 * h->nF2)) R.status = LSG_ERR_NOT_CONVERGED;
+        if (derr != LSG_OK) R.status = derr;
+        R.phase = 2;
+        *finished = true;
+        return R.status;
+    }
+    if (h->done || R.launched >= R.kmax) {
+        // true residual in FP64, then finish
+        LSG_TRY(apply_K(c, R.x, c->wv, nullptr, s));
+        ::lsg::count_launch();
+        k_true<<<kRedBlocks, kRedThreads, 0, s>>>(c->g.n, R.F, c->wv, c->red, c->counters + 4, c->st);
+        LSG_CK(cudaGetLastError());
+        R.phase = 1;
+        return snapshot(R, s);
+    }
+    int m = std::min(R.chunk, R.kmax - R.launched);
+    for (int it = 0; it < m; ++it) LSG_TRY(iteration(c, R.x, s));
+    R.launched += m;
+    R.chunk = std::min(R.chunk * 2, 32);
+    return snapshot(R, s);
+}
+
+void pcg_info(const PcgRun &R, lsg_info *info)
+{
+    if (!info) return;
+    const PcgState *h = R.c->st_host;
+    info->iters = h->k;
+    info->outer_iters = 0;
+    double nF = sqrt(h->nF2);
+    info->relres = nF > 0 ? sqrt(h->rr) / nF : sqrt(h->rr);
+    info->relres_true = nF > 0 ? sqrt(h->tr) / nF : sqrt(h->tr);
+    info->status = R.status;
+}
+
+void pcg_release(PcgRun &R)
+{
+    if (R.ev) cudaEventDestroy(R.ev);
+    R.ev = nullptr;
+}
+
+// PCG on device-resident F and x (x: initial guess in, iterate out); blocking.
+int pcg_fp64(lsg_ctx *c, const double *F, double *x, double rtol, int kmax, lsg_info *info, cudaStream_t s)
+{
+    PcgRun R{};
+    int st = pcg_start(R, c, F, x, rtol, kmax, s);
+    bool fin = false;
+    while (st == LSG_OK && !fin) st = pcg_poll(R, s, true, &fin);
+    if (fin) st = R.status;
+    pcg_info(R, info);
+    if (info) info->status = st;
+    pcg_release(R);
+    return st;
+}
+
+}  // namespace lsg

@@ -1,0 +1,433 @@
+// transform.cu -- the matrix-free product y = K x = (A + B) x of Sec. 4.3 in
+// FP64 on the GB300, as sum-factorised contractions with the basis tables.
+//
+// Sec. 4.3 evaluates K x by (1) Legendre coefficients of u_N and grad u_N,
+// (2) transforms to the Gauss grid, (3) pointwise products with a and b and
+// transforms back, (4) recombination into the phi basis.  Steps 1+2 and 3+4
+// are each one linear map per direction: contraction with the tables
+// Phi[q][k] = phi_k(x_q) and D[q][k] = phi'_k(x_q) (forward) and their
+// transposes (backward).  With Q-point Gauss quadrature this is exactly the
+// quadrature Galerkin matrix; the kernels below apply it direction by
+// direction ("contract the fastest axis, write the new axis slowest"), so that
+// after d contractions the axes are back in x-fastest order.
+//
+// Parity folding: nodes are symmetric and phi_k(-x) = (-1)^k phi_k(x),
+// phi'_k(-x) = (-1)^(k+1) phi'_k(x), so every contraction splits into an even
+// and an odd half of half the length -- half the flops of the plain tables.
+#include "lsg_internal.cuh"
+
+namespace lsg {
+
+struct XfTerm {
+    const double *x;
+    int tab;  // 0: phi (mirror sign +1), 1: phi' (mirror sign -1)
+};
+struct XfOut {
+    double *y;
+    const double *scale;  // optional pointwise factor at the output (W a or W b)
+    int nterm;
+    XfTerm t[2];
+};
+struct XfJob {
+    int nout;
+    XfOut o[4];
+    long long B;     // batch: product of the untouched axes (output row length)
+    int Q, Qh, n1, KP;
+    const double *tabE[2], *tabO[2];  // [QhP][KP]
+    const int *done;                  // optional: skip when *done != 0
+};
+
+constexpr int XT = 256;  // threads per transform CTA
+
+// Forward: coefficients (fastest axis, length n1) -> grid values (new slowest
+// axis, length Q).  out[q][b] = sum_k T[q][k] x[b][k] for the term's table T.
+// Tile: TP half-nodes x TB batch columns; 16x16 threads, each RP x RB outputs
+// for the even and the odd half.
+template <int TP, int TB, int TK>
+__global__ void __launch_bounds__(XT) k_xf_fwd(const __grid_constant__ XfJob job)
+{
+    if (job.done && *job.done) return;
+    const XfOut &O = job.o[blockIdx.z];
+    constexpr int RP = TP / 16, RB = TB / 16;
+    __shared__ double sAe[TK][TP + 1], sAo[TK][TP + 1];
+    __shared__ double sXe[TK][TB + 1], sXo[TK][TB + 1];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int p0 = blockIdx.x * TP;
+    const long long b0 = (long long)blockIdx.y * TB;
+    const XfTerm tm = O.t[0];
+    const double *TE = job.tabE[tm.tab], *TO = job.tabO[tm.tab];
+    const int n1 = job.n1, KP = job.KP;
+    const long long B = job.B;
+
+    double ae[RP][RB], ao[RP][RB];
+#pragma unroll
+    for (int i = 0; i < RP; ++i)
+#pragma unroll
+        for (int j = 0; j < RB; ++j) ae[i][j] = ao[i][j] = 0.0;
+
+    const int ne = (n1 + 1) / 2;
+    for (int m0 = 0; m0 < ne; m0 += TK) {
+        // tables: [p][m] rows padded to QhP, columns to KP (zeros)
+        for (int idx = tid; idx < TK * TP; idx += XT) {
+            int mm = idx % TK, pp = idx / TK;
+            size_t off = (size_t)(p0 + pp) * KP + (m0 + mm);
+            sAe[mm][pp] = TE[off];
+            sAo[mm][pp] = TO[off];
+        }
+        // input: x[b][a] with a in [2 m0, 2 m0 + 2 TK), split even/odd
+        for (int idx = tid; idx < 2 * TK * TB; idx += XT) {
+            int aa = idx % (2 * TK), bb = idx / (2 * TK);
+            int a = 2 * m0 + aa;
+            long long b = b0 + bb;
+            double v = (b < B && a < n1) ? tm.x[b * n1 + a] : 0.0;
+            if (aa & 1)
+                sXo[aa >> 1][bb] = v;
+            else
+                sXe[aa >> 1][bb] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; ++kk) {
+            double re[RP], ro[RP], ce[RB], co[RB];
+#pragma unroll
+            for (int i = 0; i < RP; ++i) {
+                re[i] = sAe[kk][ty + 16 * i];
+                ro[i] = sAo[kk][ty + 16 * i];
+            }
+#pragma unroll
+            for (int j = 0; j < RB; ++j) {
+                ce[j] = sXe[kk][tx + 16 * j];
+                co[j] = sXo[kk][tx + 16 * j];
+            }
+#pragma unroll
+            for (int i = 0; i < RP; ++i)
+#pragma unroll
+                for (int j = 0; j < RB; ++j) {
+                    ae[i][j] = fma(re[i], ce[j], ae[i][j]);
+                    ao[i][j] = fma(ro[i], co[j], ao[i][j]);
+                }
+        }
+        __syncthreads();
+    }
+    const double sg = tm.tab ? -1.0 : 1.0;
+    const int Q = job.Q, Qh = job.Qh;
+#pragma unroll
+    for (int i = 0; i < RP; ++i) {
+        int p = p0 + ty + 16 * i;
+        if (p >= Qh) continue;
+        int q1 = p, q2 = Q - 1 - p;
+#pragma unroll
+        for (int j = 0; j < RB; ++j) {
+            long long b = b0 + tx + 16 * j;
+            if (b >= B) continue;
+            double v1 = ae[i][j] + ao[i][j];
+            double v2 = sg * (ae[i][j] - ao[i][j]);
+            if (O.scale) {
+                v1 *= O.scale[(size_t)q1 * B + b];
+                v2 *= O.scale[(size_t)q2 * B + b];
+            }
+            O.y[(size_t)q1 * B + b] = v1;
+            if (q2 != q1) O.y[(size_t)q2 * B + b] = v2;
+        }
+    }
+}
+
+// Backward: grid values (fastest axis, length Q) -> coefficients (new slowest
+// axis, length n1).  out[k][b] = sum_terms sum_q T[q][k] x[b][q]; the input is
+// folded on load into x[q] + s x[Q-1-q] (even k) and x[q] - s x[Q-1-q] (odd k).
+template <int TM, int TB, int TK>
+__global__ void __launch_bounds__(XT) k_xf_bwd(const __grid_constant__ XfJob job)
+{
+    if (job.done && *job.done) return;
+    const XfOut &O = job.o[blockIdx.z];
+    constexpr int RM = TM / 16, RB = TB / 16;
+    __shared__ double sTe[TK][TM + 1], sTo[TK][TM + 1];
+    __shared__ double sP[TK][TB + 1], sM[TK][TB + 1];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.x * TM;
+    const long long b0 = (long long)blockIdx.y * TB;
+    const int Q = job.Q, Qh = job.Qh, KP = job.KP;
+    const long long B = job.B;
+
+    double ae[RM][RB], ao[RM][RB];
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+        for (int j = 0; j < RB; ++j) ae[i][j] = ao[i][j] = 0.0;
+
+    for (int term = 0; term < O.nterm; ++term) {
+        const XfTerm tm = O.t[term];
+        const double *TE = job.tabE[tm.tab], *TO = job.tabO[tm.tab];
+        const double sg = tm.tab ? -1.0 : 1.0;
+        for (int q0 = 0; q0 < Qh; q0 += TK) {
+            for (int idx = tid; idx < TK * TM; idx += XT) {
+                int mm = idx % TM, qq = idx / TM;
+                size_t off = (size_t)(q0 + qq) * KP + (m0 + mm);
+                sTe[qq][mm] = TE[off];
+                sTo[qq][mm] = TO[off];
+            }
+            for (int idx = tid; idx < TK * TB; idx += XT) {
+                int qq = idx % TK, bb = idx / TK;
+                int q = q0 + qq, q2 = Q - 1 - q;
+                long long b = b0 + bb;
+                double v1 = 0.0, v2 = 0.0;
+                if (q < Qh && b < B) {
+                    v1 = tm.x[b * Q + q];
+                    if (q2 != q) v2 = tm.x[b * Q + q2];
+                }
+                sP[qq][bb] = v1 + sg * v2;
+                sM[qq][bb] = v1 - sg * v2;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < TK; ++kk) {
+                double re[RM], ro[RM], cp[RB], cm[RB];
+#pragma unroll
+                for (int i = 0; i < RM; ++i) {
+                    re[i] = sTe[kk][ty + 16 * i];
+                    ro[i] = sTo[kk][ty + 16 * i];
+                }
+#pragma unroll
+                for (int j = 0; j < RB; ++j) {
+                    cp[j] = sP[kk][tx + 16 * j];
+                    cm[j] = sM[kk][tx + 16 * j];
+                }
+#pragma unroll
+                for (int i = 0; i < RM; ++i)
+#pragma unroll
+                    for (int j = 0; j < RB; ++j) {
+                        ae[i][j] = fma(re[i], cp[j], ae[i][j]);
+                        ao[i][j] = fma(ro[i], cm[j], ao[i][j]);
+                    }
+            }
+            __syncthreads();
+        }
+    }
+    const int n1 = job.n1;
+#pragma unroll
+    for (int i = 0; i < RM; ++i) {
+        int m = m0 + ty + 16 * i;
+        int ke = 2 * m, ko = 2 * m + 1;
+#pragma unroll
+        for (int j = 0; j < RB; ++j) {
+            long long b = b0 + tx + 16 * j;
+            if (b >= B) continue;
+            if (ke < n1) O.y[(size_t)ke * B + b] = ae[i][j];
+            if (ko < n1) O.y[(size_t)ko * B + b] = ao[i][j];
+        }
+    }
+}
+
+static void job_init(XfJob &j, const lsg_ctx *c, long long B, const int *done)
+{
+    const Geom &g = c->g;
+    j.nout = 0;
+    j.B = B;
+    j.Q = g.Q;
+    j.Qh = g.Qh;
+    j.n1 = g.n1;
+    j.KP = g.KP;
+    size_t blk = (size_t)g.QhP * g.KP;
+    j.tabE[0] = c->tab;
+    j.tabO[0] = c->tab + blk;
+    j.tabE[1] = c->tab + 2 * blk;
+    j.tabO[1] = c->tab + 3 * blk;
+    j.done = done;
+}
+static void add_out(XfJob &j, double *y, const double *scale, const double *x0, int t0,
+                    const double *x1 = nullptr, int t1 = 0)
+{
+    XfOut &o = j.o[j.nout++];
+    o.y = y;
+    o.scale = scale;
+    o.nterm = x1 ? 2 : 1;
+    o.t[0] = XfTerm{x0, t0};
+    o.t[1] = XfTerm{x1, t1};
+}
+
+static int launch_fwd(const XfJob &j, cudaStream_t s)
+{
+    constexpr int TP = 32, TB = 64, TK = 16;
+    dim3 grid((j.Qh + TP - 1) / TP, (unsigned)((j.B + TB - 1) / TB), j.nout);
+    ::lsg::count_launch();
+    k_xf_fwd<TP, TB, TK><<<grid, XT, 0, s>>>(j);
+    LSG_CK(cudaGetLastError());
+    return LSG_OK;
+}
+static int launch_bwd(const XfJob &j, cudaStream_t s)
+{
+    int ne = (j.n1 + 1) / 2;
+    if (j.B >= 2048) {
+        constexpr int TM = 32, TB = 64, TK = 16;
+        dim3 grid((ne + TM - 1) / TM, (unsigned)((j.B + TB - 1) / TB), j.nout);
+        ::lsg::count_launch();
+        k_xf_bwd<TM, TB, TK><<<grid, XT, 0, s>>>(j);
+    } else {
+        constexpr int TM = 32, TB = 32, TK = 16;
+        dim3 grid((ne + TM - 1) / TM, (unsigned)((j.B + TB - 1) / TB), j.nout);
+        ::lsg::count_launch();
+        k_xf_bwd<TM, TB, TK><<<grid, XT, 0, s>>>(j);
+    }
+    LSG_CK(cudaGetLastError());
+    return LSG_OK;
+}
+
+size_t workspace_elems(const Geom &g)
+{
+    size_t Q = g.Q, n1 = g.n1;
+    if (g.d == 1) return 4 * Q + 2 * n1;
+    if (g.d == 2) return 2 * Q * n1 + 3 * Q * Q;
+    return 2 * Q * n1 * n1 + 3 * Q * Q * n1 + 4 * Q * Q * Q;
+}
+
+// y = K x (Sec. 4.3), every stage on the device.  `done` (optional) makes every
+// kernel a no-op once a device-side PCG has converged.
+int apply_K(lsg_ctx *c, const double *x, double *y, const int *done, cudaStream_t s)
+{
+    const Geom &g = c->g;
+    const long long Q = g.Q, n1 = g.n1;
+    double *ws = c->ws;
+    XfJob j;
+    if (g.d == 1) {
+        double *H = ws, *Gx = ws + Q;
+        job_init(j, c, 1, done);
+        add_out(j, H, c->Wb, x, 0);
+        add_out(j, Gx, c->Wa, x, 1);
+        LSG_TRY(launch_fwd(j, s));
+        job_init(j, c, 1, done);
+        add_out(j, y, nullptr, H, 0, Gx, 1);
+        return launch_bwd(j, s);
+    }
+    if (g.d == 2) {
+        double *AP = ws, *AD = ws + Q * n1;           // [Q][n1]
+        double *H = ws + 2 * Q * n1, *Gy = H + Q * Q, *Gx = Gy + Q * Q;  // [Q][Q]
+        double *P1 = AP, *P2 = AD;                    // [n1][Q] (reuse)
+        job_init(j, c, n1, done);                     // contract x: U[j][k]
+        add_out(j, AP, nullptr, x, 0);
+        add_out(j, AD, nullptr, x, 1);
+        LSG_TRY(launch_fwd(j, s));
+        job_init(j, c, Q, done);                      // contract y: A[q][j]
+        add_out(j, H, c->Wb, AP, 0);
+        add_out(j, Gy, c->Wa, AP, 1);
+        add_out(j, Gx, c->Wa, AD, 0);
+        LSG_TRY(launch_fwd(j, s));
+        job_init(j, c, Q, done);                      // contract x-nodes: [r][q]
+        add_out(j, P1, nullptr, H, 0, Gx, 1);
+        add_out(j, P2, nullptr, Gy, 0);
+        LSG_TRY(launch_bwd(j, s));
+        job_init(j, c, n1, done);                     // contract y-nodes: [m][r]
+        add_out(j, y, nullptr, P1, 0, P2, 1);
+        return launch_bwd(j, s);
+    }
+    // d == 3
+    double *A0 = ws, *A1 = ws + Q * n1 * n1;                       // [Q][n1][n1]
+    double *B0 = ws + 2 * Q * n1 * n1, *B1 = B0 + Q * Q * n1, *B2 = B1 + Q * Q * n1;  // [Q][Q][n1]
+    double *F0 = B2 + Q * Q * n1, *F1 = F0 + Q * Q * Q, *F2 = F1 + Q * Q * Q, *F3 = F2 + Q * Q * Q;
+    double *H = F0, *Gz = F1, *Gy = F2, *Gx = F3;
+    job_init(j, c, n1 * n1, done);                 // x: U[l][j][k] -> [q][l][j]
+    add_out(j, A0, nullptr, x, 0);
+    add_out(j, A1, nullptr, x, 1);
+    LSG_TRY(launch_fwd(j, s));
+    job_init(j, c, Q * n1, done);                  // y: [q][l][j] -> [r][q][l]
+    add_out(j, B0, nullptr, A0, 0);                // phi_x phi_y
+    add_out(j, B1, nullptr, A0, 1);                // phi_x phi'_y
+    add_out(j, B2, nullptr, A1, 0);                // phi'_x phi_y
+    LSG_TRY(launch_fwd(j, s));
+    job_init(j, c, Q * Q, done);                   // z: [r][q][l] -> [s][r][q]
+    add_out(j, H, c->Wb, B0, 0);
+    add_out(j, Gz, c->Wa, B0, 1);
+    add_out(j, Gy, c->Wa, B1, 0);
+    add_out(j, Gx, c->Wa, B2, 0);
+    LSG_TRY(launch_fwd(j, s));
+    double *Pa = B0, *Pb = B1, *Pc = B2;           // [n1][Q][Q] = [m][s][r]
+    job_init(j, c, Q * Q, done);
+    add_out(j, Pa, nullptr, H, 0, Gx, 1);
+    add_out(j, Pb, nullptr, Gy, 0);
+    add_out(j, Pc, nullptr, Gz, 0);
+    LSG_TRY(launch_bwd(j, s));
+    double *Ra = A0, *Rc = A1;                     // [n1][n1][Q] = [n'][m][s]
+    job_init(j, c, n1 * Q, done);
+    add_out(j, Ra, nullptr, Pa, 0, Pb, 1);
+    add_out(j, Rc, nullptr, Pc, 0);
+    LSG_TRY(launch_bwd(j, s));
+    job_init(j, c, n1 * n1, done);                 // [l'][n'][m]
+    add_out(j, y, nullptr, Ra, 0, Rc, 1);
+    return launch_bwd(j, s);
+}
+
+__global__ void k_mul(long long n, const double *a, const double *b, double *out)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[i] * b[i];
+}
+
+// F = sum_grid W f Psi_k: the backward contractions with the phi tables only.
+int load_vector(lsg_ctx *c, const double *f, double *F, cudaStream_t s)
+{
+    const Geom &g = c->g;
+    const long long Q = g.Q, n1 = g.n1;
+    double *ws = c->ws;
+    double *G = ws + workspace_elems(g) - g.nq;  // W f at the end of the workspace
+    ::lsg::count_launch();
+    k_mul<<<(unsigned)((g.nq + 255) / 256), 256, 0, s>>>(g.nq, c->Wg, f, G);
+    LSG_CK(cudaGetLastError());
+    XfJob j;
+    if (g.d == 1) {
+        job_init(j, c, 1, nullptr);
+        add_out(j, F, nullptr, G, 0);
+        return launch_bwd(j, s);
+    }
+    if (g.d == 2) {
+        double *P = ws;
+        job_init(j, c, Q, nullptr);
+        add_out(j, P, nullptr, G, 0);
+        LSG_TRY(launch_bwd(j, s));
+        job_init(j, c, n1, nullptr);
+        add_out(j, F, nullptr, P, 0);
+        return launch_bwd(j, s);
+    }
+    double *P = ws, *R = ws + n1 * Q * Q;
+    job_init(j, c, Q * Q, nullptr);
+    add_out(j, P, nullptr, G, 0);
+    LSG_TRY(launch_bwd(j, s));
+    job_init(j, c, n1 * Q, nullptr);
+    add_out(j, R, nullptr, P, 0);
+    LSG_TRY(launch_bwd(j, s));
+    job_init(j, c, n1 * n1, nullptr);
+    add_out(j, F, nullptr, R, 0);
+    return launch_bwd(j, s);
+}
+
+// u_N at the grid: the forward contractions with the phi tables only.
+int eval_grid(lsg_ctx *c, const double *u, double *vals, cudaStream_t s)
+{
+    const Geom &g = c->g;
+    const long long Q = g.Q, n1 = g.n1;
+    double *ws = c->ws;
+    XfJob j;
+    if (g.d == 1) {
+        job_init(j, c, 1, nullptr);
+        add_out(j, vals, nullptr, u, 0);
+        return launch_fwd(j, s);
+    }
+    if (g.d == 2) {
+        job_init(j, c, n1, nullptr);
+        add_out(j, ws, nullptr, u, 0);
+        LSG_TRY(launch_fwd(j, s));
+        job_init(j, c, Q, nullptr);
+        add_out(j, vals, nullptr, ws, 0);
+        return launch_fwd(j, s);
+    }
+    double *A = ws, *Bv = ws + Q * n1 * n1;
+    job_init(j, c, n1 * n1, nullptr);
+    add_out(j, A, nullptr, u, 0);
+    LSG_TRY(launch_fwd(j, s));
+    job_init(j, c, Q * n1, nullptr);
+    add_out(j, Bv, nullptr, A, 0);
+    LSG_TRY(launch_fwd(j, s));
+    job_init(j, c, Q * Q, nullptr);
+    add_out(j, vals, nullptr, Bv, 0);
+    return launch_fwd(j, s);
+}
+
+}  // namespace lsg
