@@ -119,6 +119,21 @@ long long lsg_kernel_launches(void);
  * (Sec. 2.1).  x, w: host arrays of Q doubles.  Q >= 1. */
 int lsg_gauss(int Q, double *x, double *w);
 
+/* The same Gauss rule as lsg_gauss, for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a property of the library, not
+ * of the method.  lsg_gauss allocates two device buffers on every call; code that
+ * runs while the device's memory is fully reserved by another component, or
+ * under a policy that forbids allocator calls once a job has started, cannot use
+ * it.  This variant keeps that scratch in a fixed device array inside the library
+ * (room for Q <= 16384; 256 KiB held on every device that loads the library until
+ * the process exits) and calls no allocator.  Q > 16384 returns LSG_ERR_ARG with
+ * an explanation in lsg_last_error.  The first call on a device looks up the
+ * array's device address; make that first call before any stream capture.  Every
+ * call shares the one array and synchronises the device's default stream, so
+ * calls that overlap on the GPU (from several host threads) race on it.
+ * x, w: host arrays of Q doubles. */
+int lsg_gauss_noalloc(int Q, double *x, double *w);
+
 /* Device bytes lsg_setup_ex would allocate for these sizes (admission model). */
 size_t lsg_footprint_bytes(int d, int N, int T, int Q, int precision);
 

@@ -33,7 +33,7 @@ OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_ILU_BREAKDOWN, ERR_NOT_CONVERGED, ERR_TIME
 
 # every symbol the header declares (checked by the ABI test)
 SYMBOLS = [
-    "lsg_version", "lsg_status_string", "lsg_last_error", "lsg_kernel_launches", "lsg_gauss", "lsg_footprint_bytes",
+    "lsg_version", "lsg_status_string", "lsg_last_error", "lsg_kernel_launches", "lsg_gauss", "lsg_gauss_noalloc", "lsg_footprint_bytes",
     "lsg_setup", "lsg_setup_ex", "lsg_load_vector", "lsg_apply_A", "lsg_apply_Minv", "lsg_pcg_solve",
     "lsg_eval", "lsg_export_count", "lsg_export", "lsg_query", "lsg_destroy", "lsg_batch_solve",
     "lsg_server_create", "lsg_server_submit", "lsg_server_poll", "lsg_server_drain",
@@ -86,6 +86,7 @@ def load(build_if_needed: bool = True):
     L.lsg_last_error.restype = ctypes.c_char_p
     L.lsg_kernel_launches.restype = cll
     L.lsg_gauss.argtypes = [ci, vp, vp]
+    L.lsg_gauss_noalloc.argtypes = [ci, vp, vp]
     L.lsg_footprint_bytes.argtypes = [ci, ci, ci, ci, ci]
     L.lsg_footprint_bytes.restype = ctypes.c_size_t
     L.lsg_setup.argtypes = [ctypes.POINTER(vp), ci, ci, ci, ci, vp, vp, ci, vp]
@@ -166,6 +167,15 @@ def gauss(Q: int):
     x = np.zeros(Q)
     w = np.zeros(Q)
     _check(L.lsg_gauss(Q, _ptr(x), _ptr(w)), "lsg_gauss")
+    return x, w
+
+
+def gauss_noalloc(Q: int):
+    """Gauss rule through the entry point that allocates no device memory."""
+    L = load()
+    x = np.zeros(Q)
+    w = np.zeros(Q)
+    _check(L.lsg_gauss_noalloc(Q, _ptr(x), _ptr(w)), "lsg_gauss_noalloc")
     return x, w
 
 
