@@ -91,7 +91,7 @@ static size_t footprint(const Geom &g, int precision, unsigned flags)
     size_t b = 2 * (size_t)g.Q * 8 + z.tab + z.tab32 + 3 * z.grid + 2 * z.series + 2 * z.band + z.Lv + z.Uv +
                z.Mkeep + z.ws + 7 * z.vec + (size_t)g.n * 4 * 2 + 2 * z.lines + 64 + kRedBlocks * 16 +
                sizeof(PcgState);
-    if (precision != LSG_FP64) b += 5 * (size_t)g.n * 4 + 2 * z.vec + z.ws / 2;
+    if (precision != LSG_FP64) b += 6 * (size_t)g.n * 4 + 2 * (size_t)g.nq * 4 + 2 * z.vec + z.ws / 2;
     // transient setup buffers: sample staging (2 grids) and the precontracted arrays
     size_t T1 = g.T + 1;
     size_t nK = g.d == 3 ? T1 * T1 : T1;
@@ -148,7 +148,7 @@ static void free_ctx(lsg_ctx *c)
     void *ptrs[] = {c->gx, c->gw, c->tab, c->tab32, c->Wa, c->Wb, c->Wg, c->ahat, c->bhat, c->bandS, c->bandM,
                     c->Lv, c->Uv, c->Mkeep, c->order, c->rowflag, c->prog, c->counters, c->err, c->ws, c->ws32,
                     c->r, c->z, c->p, c->wv, c->xs, c->fs, c->ys, c->red, c->st, c->r32, c->z32, c->p32, c->w32,
-                    c->e32, c->e64, c->u64};
+                    c->e32, c->e64, c->u64, c->y32, c->Wa32, c->Wb32};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->st_host) cudaFreeHost(c->st_host);
@@ -298,6 +298,9 @@ int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, con
         ALLOC(c->p32, (size_t)g.n * 4);
         ALLOC(c->w32, (size_t)g.n * 4);
         ALLOC(c->e32, (size_t)g.n * 4);
+        ALLOC(c->y32, (size_t)g.n * 4);
+        ALLOC(c->Wa32, (size_t)g.nq * 4);
+        ALLOC(c->Wb32, (size_t)g.nq * 4);
         ALLOC(c->e64, z.vec);
         ALLOC(c->u64, z.vec);
         ALLOC(c->ws32, z.ws / 2);
@@ -427,7 +430,8 @@ int lsg_pcg_solve(lsg_ctx *c, const double *F, double *u, double rtol, int kmax,
         du = c->xs;
         LSG_CK(cudaMemcpyAsync(du, u, sizeof(double) * (size_t)c->g.n, cudaMemcpyHostToDevice, s));
     }
-    int st = pcg_fp64(c, dF, du, rtol, kmax, info, s);
+    int st = (c->precision == LSG_FP64) ? pcg_fp64(c, dF, du, rtol, kmax, info, s)
+                                        : pcg_mixed(c, dF, du, rtol, kmax, info, s);
     if (hu) {
         LSG_CK(cudaMemcpyAsync(u, du, sizeof(double) * (size_t)c->g.n, cudaMemcpyDeviceToHost, s));
         LSG_CK(cudaStreamSynchronize(s));

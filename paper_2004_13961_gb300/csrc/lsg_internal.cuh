@@ -5,7 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/lsg.h"
+#include "lsg.h"
 
 namespace lsg {
 
@@ -76,6 +76,7 @@ struct lsg_ctx {
     double *tab;               // 4 blocks of QhP*KP: phiE, phiO, dphiE, dphiO
     float *tab32;              // FP32 copies (mixed)
     double *Wa, *Wb, *Wg;      // w(x)w(y)w(z) * a, * b, and the weights alone (Q^d)
+    float *Wa32, *Wb32;        // FP32 copies (mixed)
     double *ahat, *bhat;       // (T+1)^d
     double *bandS, *bandM;     // (T+1) x n1 x W1
 
@@ -100,7 +101,7 @@ struct lsg_ctx {
     lsg::PcgState *st;         // device state
     lsg::PcgState *st_host;    // pinned mirror
     // mixed precision inner vectors
-    float *r32, *z32, *p32, *w32, *e32;
+    float *r32, *z32, *p32, *w32, *e32, *y32;
     double *e64, *u64;
 
     // setup stage times (milliseconds, CUDA events): tables, assembly, ILU(0)
@@ -117,9 +118,11 @@ bool is_device_ptr(const void *p);
 int build_tables(lsg_ctx *c, const double *a_dev, const double *b_dev, cudaStream_t s);
 int build_preconditioner(lsg_ctx *c, cudaStream_t s);
 int apply_K(lsg_ctx *c, const double *x, double *y, const int *done, cudaStream_t s);
+int apply_K32(lsg_ctx *c, const float *x, float *y, const int *done, cudaStream_t s);
 int load_vector(lsg_ctx *c, const double *f, double *F, cudaStream_t s);
 int eval_grid(lsg_ctx *c, const double *u, double *vals, cudaStream_t s);
 int apply_Minv(lsg_ctx *c, const double *r, double *z, const int *done, cudaStream_t s);
+int apply_Minv32(lsg_ctx *c, const float *r, float *z, const int *done, cudaStream_t s);
 int pcg_fp64(lsg_ctx *c, const double *F, double *u, double rtol, int kmax, lsg_info *info,
              cudaStream_t s);
 
@@ -135,6 +138,8 @@ int pcg_start(PcgRun &R, lsg_ctx *c, const double *F, double *x, double rtol, in
 int pcg_poll(PcgRun &R, cudaStream_t s, bool wait, bool *finished);
 void pcg_info(const PcgRun &R, lsg_info *info);
 void pcg_release(PcgRun &R);
+int pcg_mixed(lsg_ctx *c, const double *F, double *u, double rtol, int kmax, lsg_info *info,
+              cudaStream_t s);
 int read_dev_error(lsg_ctx *c, cudaStream_t s);
 int check_finite(lsg_ctx *c, const double *v, long long n, cudaStream_t s);
 size_t workspace_elems(const Geom &g);

@@ -335,4 +335,242 @@ int pcg_fp64(lsg_ctx *c, const double *F, double *x, double rtol, int kmax, lsg_
     return st;
 }
 
+// ---------------------------------------------------------------------------
+// Mixed precision (a FP64 refinement loop around an FP32 inner PCG).
+//
+// Outer loop in FP64: r = F - K u (FP64 transforms), stop when
+// ||r|| <= rtol ||F||; otherwise solve K e = r / ||r|| approximately with PCG
+// in FP32 (FP32 vectors, FP32 ILU(0) factors, low-precision transforms, FP64
+// dot-product accumulation) to a loose relative tolerance, and update
+// u += ||r|| e in FP64.  Residual normalisation keeps the FP32 inner problem
+// well scaled at every refinement step.
+
+__global__ void k_cast_scale(long long n, const double *r, double scale, float *r32, float *x32)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        r32[i] = (float)(r[i] * scale);
+        x32[i] = 0.f;
+    }
+}
+
+// inner start: nF2 := r.r (reference), rr = r.r, k = 0
+__global__ void __launch_bounds__(kRedThreads) k_init32(long long n, const float *r, double *red, unsigned *cnt,
+                                                       PcgState *st)
+{
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double v = r[i];
+        a += v * v;
+    }
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) red[blockIdx.x] = a;
+    if (last_block(cnt)) {
+        double rr = combine(red, 1, 0, sh);
+        if (threadIdx.x == 0) {
+            st->nF2 = rr;
+            st->rr = rr;
+            st->k = 0;
+            st->rho = 0.0;
+            st->status = LSG_OK;
+            st->done = (rr <= st->eps2 * rr || st->kmax <= 0 || rr == 0.0) ? 1 : 0;
+            *cnt = 0;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_rz32(long long n, const float *r, const float *z, double *red,
+                                                     unsigned *cnt, PcgState *st)
+{
+    if (st->done) return;
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a += (double)r[i] * (double)z[i];
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) red[blockIdx.x] = a;
+    if (last_block(cnt)) {
+        double rho = combine(red, 1, 0, sh);
+        if (threadIdx.x == 0) {
+            st->beta = (st->k == 0) ? 0.0 : rho / st->rho;
+            st->rho_old = st->rho;
+            st->rho = rho;
+            *cnt = 0;
+        }
+    }
+}
+
+__global__ void k_pupd32(long long n, const float *z, float *p, const PcgState *st)
+{
+    if (st->done) return;
+    const float beta = (float)st->beta;
+    const bool first = st->k == 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = first ? z[i] : fmaf(beta, p[i], z[i]);
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_pw32(long long n, const float *p, const float *w, double *red,
+                                                     unsigned *cnt, PcgState *st)
+{
+    if (st->done) return;
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a += (double)p[i] * (double)w[i];
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) red[blockIdx.x] = a;
+    if (last_block(cnt)) {
+        double pw = combine(red, 1, 0, sh);
+        if (threadIdx.x == 0) {
+            st->pw = pw;
+            if (!(pw > 0.0)) {
+                st->status = LSG_ERR_NOT_CONVERGED;
+                st->done = 1;
+            } else {
+                st->alpha = st->rho / pw;
+            }
+            *cnt = 0;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_xr32(long long n, float *x, float *r, const float *p, const float *w,
+                                                     double *red, unsigned *cnt, PcgState *st)
+{
+    if (st->done) return;
+    __shared__ double sh[32];
+    const float alpha = (float)st->alpha;
+    double a = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        x[i] = fmaf(alpha, p[i], x[i]);
+        float ri = fmaf(-alpha, w[i], r[i]);
+        r[i] = ri;
+        a += (double)ri * (double)ri;
+    }
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) red[blockIdx.x] = a;
+    if (last_block(cnt)) {
+        double rr = combine(red, 1, 0, sh);
+        if (threadIdx.x == 0) {
+            st->rr = rr;
+            st->k += 1;
+            if (rr <= st->eps2 * st->nF2 || st->k >= st->kmax) st->done = 1;
+            *cnt = 0;
+        }
+    }
+}
+
+__global__ void k_update64(long long n, double *u, const float *e, double scale)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        u[i] += scale * (double)e[i];
+}
+
+static int iteration32(lsg_ctx *c, cudaStream_t s)
+{
+    const long long n = c->g.n;
+    const int *done = &c->st->done;
+    unsigned *cnt = c->counters + 4;
+    LSG_TRY(apply_Minv32(c, c->r32, c->z32, done, s));
+    ::lsg::count_launch();
+    k_rz32<<<kRedBlocks, kRedThreads, 0, s>>>(n, c->r32, c->z32, c->red, cnt, c->st);
+    ::lsg::count_launch();
+    k_pupd32<<<kRedBlocks, kRedThreads, 0, s>>>(n, c->z32, c->p32, c->st);
+    LSG_TRY(apply_K32(c, c->p32, c->w32, done, s));
+    ::lsg::count_launch();
+    k_pw32<<<kRedBlocks, kRedThreads, 0, s>>>(n, c->p32, c->w32, c->red, cnt, c->st);
+    ::lsg::count_launch();
+    k_xr32<<<kRedBlocks, kRedThreads, 0, s>>>(n, c->e32, c->r32, c->p32, c->w32, c->red, cnt, c->st);
+    LSG_CK(cudaGetLastError());
+    return LSG_OK;
+}
+
+// r = F - K u in FP64 and its norm; returns rr and nF2 on the host.
+static int outer_residual(lsg_ctx *c, const double *F, const double *u, double *rr, double *nF2, cudaStream_t s)
+{
+    PcgState *h = c->st_host;
+    LSG_TRY(apply_K(c, u, c->wv, nullptr, s));
+    ::lsg::count_launch();
+    k_init<<<kRedBlocks, kRedThreads, 0, s>>>(c->g.n, F, c->wv, c->r, c->red, c->counters + 4, c->st);
+    LSG_CK(cudaGetLastError());
+    LSG_CK(cudaMemcpyAsync(h, c->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    LSG_CK(cudaStreamSynchronize(s));
+    *rr = h->rr;
+    *nF2 = h->nF2;
+    return LSG_OK;
+}
+
+int pcg_mixed(lsg_ctx *c, const double *F, double *u, double rtol, int kmax, lsg_info *info, cudaStream_t s)
+{
+    const long long n = c->g.n;
+    PcgState *h = c->st_host;
+    // inner relative tolerance: a few digits per refinement step is enough; the
+    // low-precision operator limits what one inner solve can deliver anyway
+    const double inner_tol = (c->precision == LSG_MIXED_BF16) ? 1e-3 : 1e-4;
+    const int max_outer = 40;
+    *h = PcgState{};
+    h->eps2 = rtol * rtol;
+    h->kmax = 1;
+    LSG_CK(cudaMemcpyAsync(c->st, h, sizeof(PcgState), cudaMemcpyHostToDevice, s));
+    LSG_CK(cudaMemsetAsync(c->counters + 4, 0, sizeof(unsigned), s));
+    double rr = 0.0, nF2 = 0.0;
+    LSG_TRY(outer_residual(c, F, u, &rr, &nF2, s));
+    int total = 0, outer = 0, status = LSG_OK;
+    double last_inner = 0.0;
+    while (!(rr <= rtol * rtol * nF2)) {
+        if (outer >= max_outer || total >= kmax) {
+            status = LSG_ERR_NOT_CONVERGED;
+            break;
+        }
+        const double rn = sqrt(rr);
+        ::lsg::count_launch();
+        k_cast_scale<<<kRedBlocks, kRedThreads, 0, s>>>(n, c->r, 1.0 / rn, c->r32, c->e32);
+        h->eps2 = inner_tol * inner_tol;
+        h->kmax = kmax - total;
+        h->done = 0;
+        LSG_CK(cudaMemcpyAsync(&c->st->eps2, &h->eps2, sizeof(double), cudaMemcpyHostToDevice, s));
+        LSG_CK(cudaMemcpyAsync(&c->st->kmax, &h->kmax, sizeof(int), cudaMemcpyHostToDevice, s));
+        ::lsg::count_launch();
+        k_init32<<<kRedBlocks, kRedThreads, 0, s>>>(n, c->r32, c->red, c->counters + 4, c->st);
+        LSG_CK(cudaGetLastError());
+        int chunk = 4, launched = 0;
+        for (;;) {
+            LSG_CK(cudaMemcpyAsync(h, c->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+            LSG_CK(cudaStreamSynchronize(s));
+            if (h->done || launched >= kmax - total) break;
+            int e = read_dev_error(c, s);
+            if (e != LSG_OK) return e;
+            int m = std::min(chunk, kmax - total - launched);
+            for (int it = 0; it < m; ++it) LSG_TRY(iteration32(c, s));
+            launched += m;
+            chunk = std::min(chunk * 2, 32);
+        }
+        total += h->k;
+        last_inner = h->nF2 > 0 ? sqrt(h->rr / h->nF2) : 0.0;
+        int e = read_dev_error(c, s);
+        if (e != LSG_OK) return e;
+        if (h->k == 0) {
+            status = LSG_ERR_NOT_CONVERGED;
+            break;
+        }
+        ::lsg::count_launch();
+        k_update64<<<kRedBlocks, kRedThreads, 0, s>>>(n, u, c->e32, rn);
+        double prev = rr;
+        LSG_TRY(outer_residual(c, F, u, &rr, &nF2, s));
+        ++outer;
+        if (!(rr < 0.99 * prev) && !(rr <= rtol * rtol * nF2)) {
+            status = LSG_ERR_NOT_CONVERGED;  // refinement stagnated
+            break;
+        }
+    }
+    if (info) {
+        info->iters = total;
+        info->outer_iters = outer;
+        info->relres = last_inner;
+        info->relres_true = nF2 > 0 ? sqrt(rr / nF2) : sqrt(rr);
+        info->status = status;
+    }
+    return status;
+}
+
 }  // namespace lsg

@@ -3,60 +3,61 @@
 // substitution with the upper factor (Algorithm 4), on the stencil storage.
 //
 // Dependency structure (natural order, stencil half-width w): row (i,j,k)
-// needs every lower neighbour; the newest ones are (i-1,j,k) and (i+w,j-1,k)
-// (and (i+w,j+w,k-1) in 3D), one wavefront level earlier.  A line (fixed j,k)
-// is therefore a chain whose position i may only be finished after the
-// previous line (j-1,k) has finished position i+w.
+// needs its lower neighbours; the newest are (i-1,j,k) and (i+w,j-1,k) (and
+// (i+w,j+w,k-1) in 3D).  A line (fixed j,k) is a chain whose position i may
+// be finished once the previous line has finished position i+w.
 //
-// Kernel design (GB300): a CTA owns a band of B consecutive lines and runs two
-// warps per line.
-//   * The bulk warp streams the line's factor rows through a cp.async ring in
-//     shared memory and, for each row, sums every entry except the K newest
-//     ones of its own line and of the previous line (the "late" entries); it
-//     hands the row over through a small record ring (bulk sum, right-hand
-//     side, the late factor values, the inverse pivot).
-//   * The finaliser warp applies only the <= 2K late entries, reading the
-//     solution values of its own and the previous line from shared memory,
-//     so the chain from one wavefront level to the next is a few shared-memory
-//     operations instead of a full dot product and reduction.
-// Lines of the band exchange values and progress through shared memory; bands
-// exchange them through global memory (values) and release/acquire progress
-// words, published by the bulk warps.  Bands are claimed in sweep order, so a
-// CTA only ever waits for lines claimed earlier by a running CTA.  Every wait
-// is bounded and reports LSG_ERR_TIMEOUT through the device error word.
+// Kernel design (GB300).  A CTA owns a band of B consecutive lines, one
+// compute warp per line, and runs in lockstep ticks: at tick t, line b
+// finishes its row t - (w+1) b.  Every value that row needs was finished at a
+// tick <= t-1 (own line: previous position; line b-1: position + w; older
+// lines and the halo further back), so a tick is a dot product per warp, a
+// warp reduction and one named barrier -- no waits between the lines of a
+// band.  All data movement is done by three helper warps, off the tick's
+// critical path:
+//   * a TMA producer streams factor rows into a per-line ring in shared memory
+//     with bulk copies (cp.async.bulk) that complete on mbarriers, D rows ahead
+//     of the tick that consumes them;
+//   * a halo loader stages the w lines before the band (finished by the
+//     previous band) into shared memory with 16-byte cp.async copies as soon
+//     as their progress words allow, and publishes how far the halo is ready;
+//   * a publisher copies finished values to global memory and releases
+//     per-line progress words.
+// The compute warps keep their stencil offsets in registers and read padded,
+// zero-initialised row buffers, so the 1D/2D dot product has no branches: a
+// slot outside the grid carries an exact-zero factor.  In 3D, neighbours in
+// other planes are read from global memory after the plane's progress word is
+// acquired.  Bands are claimed in sweep order, so a CTA only waits for lines
+// claimed earlier by a running CTA; every wait is bounded and reports
+// LSG_ERR_TIMEOUT through the device error word.
 #include "stencil.cuh"
 
 namespace lsg {
 
-constexpr int SW_MAXB = 8;          // lines per CTA (two warps each)
-constexpr int SW_K = 4;             // late depth (clamped to w)
-constexpr int SW_R = 16;            // record ring depth (rows a bulk warp may run ahead)
-constexpr int SW_LATE = 2 * SW_K;   // late entries per row
-constexpr int SW_PUB = 8;           // rows between global progress publications
+constexpr int SW_MAXB = 8;   // compute warps (lines) per CTA
+constexpr int SW_HELP = 3;   // helper warps: TMA producer, halo loader, publisher
+constexpr int SW_D = 6;      // factor ring depth (rows in flight per line)
+constexpr int SW_PUB = 4;    // positions between progress publications
+constexpr int SW_KS = 16;    // register-resident slots per lane (1D/2D path)
 
 struct SweepArgs {
     StencilGeo G;
     const void *F;       // factor rows: Lv (forward) or Uv (backward)
-    int RL;              // row length of F (elements)
-    const double *rhs;
-    double *out;
-    unsigned *gprog;     // per line progress in sweep order (virtual positions finished)
+    int RL;              // row length of F (elements); RL * sizeof(V) is a multiple of 16
+    const void *rhs;     // AT[n]
+    void *out;           // AT[n]
+    unsigned *gprog;     // per line progress in sweep order (positions finished)
     unsigned *counter;   // band claim counter
     const int *done;
     int *err;
     int B;               // lines per CTA
-    int K;               // late depth
 };
 
+// ---- asynchronous copy and mbarrier primitives (inline PTX, sm_90+) --------
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc)
 {
-    unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc)
-{
-    unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gsrc) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -64,16 +65,64 @@ __device__ __forceinline__ void cp_async_wait()
 {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
-
-// Bounded spin on a shared-memory progress word.  Only SM-local state is read
-// while spinning (a producer in this CTA that gives up releases its dependants
-// itself), so a satisfied wait costs no off-SM round trip.
-__device__ __forceinline__ bool spin_smem(volatile unsigned *p, unsigned need, int *err)
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
 {
-    if (*p >= need) return true;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// TMA bulk copy global -> shared, completion counted on an mbarrier.
+__device__ __forceinline__ void tma_load(void *sdst, const void *gsrc, unsigned bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(sdst)),
+        "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void named_barrier(int id, int threads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Bounded wait for an mbarrier phase (every lane polls, so each gets acquire order).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int *err)
+{
+    if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     for (;;) {
-        if (*p >= need) return true;
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > kSpinBudgetCycles) {
+            set_err(err, DERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// Bounded spin until a shared word reaches `need` (sleeping between polls).
+__device__ __forceinline__ bool wait_smem_at_least(const unsigned *w, unsigned need, const volatile int *abort_flag,
+                                                   int *err)
+{
+    if (*(volatile const unsigned *)w >= need) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        __nanosleep(20);
+        if (*(volatile const unsigned *)w >= need) return true;
+        if (*abort_flag) return false;
         if (clock64() - t0 > kSpinBudgetCycles) {
             set_err(err, DERR_TIMEOUT);
             return false;
@@ -82,286 +131,369 @@ __device__ __forceinline__ bool spin_smem(volatile unsigned *p, unsigned need, i
 }
 
 struct SweepSmem {
-    size_t sy, rbulk, rrhs, rdiag, rlate, rhsring, ring, meta, total;
+    size_t rowoff, sy, srhs, ring, mbar, meta, total;
+    int RS;    // row stride (elements) of the value buffers
+    int PADL;  // left padding (elements) before position 0
 };
 
-__host__ __device__ inline SweepSmem sweep_layout(int n1, int B, int D, int RL, int vsize, int nslot)
+__host__ __device__ inline SweepSmem sweep_layout(int n1, int w, int B, int RL, int vsize, int nslot, int asize)
 {
     SweepSmem L;
+    const int ce = 16 / asize;                          // elements per 16-byte chunk
+    L.PADL = ((w + ce - 1) / ce + 1) * ce;              // room for i+dx >= -w and chunk alignment
+    L.RS = ((L.PADL + n1 + w + 2 * ce + ce - 1) / ce) * ce;
     size_t o = 0;
-    L.sy = o;      o += (size_t)B * n1 * 8;
-    L.rbulk = o;   o += (size_t)B * SW_R * 8;
-    L.rrhs = o;    o += (size_t)B * SW_R * 8;
-    L.rdiag = o;   o += (size_t)B * SW_R * 8;
-    L.rlate = o;   o += (size_t)B * SW_R * SW_LATE * 8;
-    L.rhsring = o; o += (size_t)B * D * 8;
+    L.rowoff = o;  o += (size_t)(w + SW_MAXB) * 4;
     o = (o + 127) / 128 * 128;
-    L.ring = o;    o += (size_t)B * D * RL * vsize;
+    L.sy = o;      o += (size_t)(w + B) * L.RS * asize;
+    o = (o + 15) / 16 * 16;
+    L.srhs = o;    o += (size_t)B * n1 * asize;
+    o = (o + 127) / 128 * 128;
+    L.ring = o;    o += (size_t)B * SW_D * RL * vsize;
+    o = (o + 7) / 8 * 8;
+    L.mbar = o;    o += (size_t)B * SW_D * 8;
     L.meta = o;    o += (size_t)nslot * 4;
     L.total = o;
     return L;
 }
 
-template <typename V, int DIR, int D>
-__global__ void __launch_bounds__(64 * SW_MAXB) k_sweep(const __grid_constant__ SweepArgs A)
+template <typename V, typename AT, int DIR>
+__global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid_constant__ SweepArgs A)
 {
     if (A.done && *A.done) return;
     const StencilGeo G = A.G;
-    const int n1 = G.n1, w = G.w, B = A.B, K = A.K, RL = A.RL;
+    const int n1 = G.n1, w = G.w, B = A.B, RL = A.RL;
     const int nslot = G.Sc;
     extern __shared__ __align__(128) unsigned char smem[];
-    const SweepSmem Lo = sweep_layout(n1, B, D, RL, (int)sizeof(V), nslot);
-    volatile double *sy = (volatile double *)(smem + Lo.sy);
-    volatile double *rbulk = (volatile double *)(smem + Lo.rbulk);
-    volatile double *rrhs = (volatile double *)(smem + Lo.rrhs);
-    volatile double *rdiag = (volatile double *)(smem + Lo.rdiag);
-    volatile double *rlate = (volatile double *)(smem + Lo.rlate);
-    double *rhsring = (double *)(smem + Lo.rhsring);
+    const SweepSmem Lo = sweep_layout(n1, w, B, RL, (int)sizeof(V), nslot, (int)sizeof(AT));
+    const int RS = Lo.RS, PADL = Lo.PADL;
+    int *rowoff = (int *)(smem + Lo.rowoff);
+    AT *sy = (AT *)(smem + Lo.sy);
+    AT *srhs = (AT *)(smem + Lo.srhs);
     V *ring = (V *)(smem + Lo.ring);
+    uint64_t *mbar = (uint64_t *)(smem + Lo.mbar);
     unsigned *meta = (unsigned *)(smem + Lo.meta);
-    __shared__ volatile unsigned fin_prog[SW_MAXB], bulk_prog[SW_MAXB];
+    __shared__ volatile int s_abort;
+    __shared__ unsigned s_tick;      // ticks finished by the compute warps
+    __shared__ unsigned s_halo;      // virtual positions of every halo line staged in shared memory
     __shared__ long long sband;
+    __shared__ int s_issued[SW_MAXB];  // factor rows the producer issued per line (this band)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const bool is_bulk = wid < B;
-    const int b = is_bulk ? wid : wid - B;
+    const int role = wid - B;  // < 0: compute warp; 0: TMA producer; 1: halo loader; 2: publisher
+    const AT *rhs = (const AT *)A.rhs;
+    AT *out = (AT *)A.out;
     const V *F = (const V *)A.F;
+    constexpr int CE = 16 / (int)sizeof(AT);
+    const bool regpath = G.d < 3 && nslot <= 32 * SW_KS;
 
-    // slot table: offsets and late class, in virtual (sweep-direction) terms
     for (int t = threadIdx.x; t < nslot; t += blockDim.x) {
         int s = DIR > 0 ? t : G.Sc + 1 + t;
         int dx, dy, dz;
         slot_offsets(G, s, dx, dy, dz);
-        int vx = DIR * dx, vy = DIR * dy, vz = DIR * dz;
-        unsigned cls = 0;
-        if (vy == 0 && vz == 0 && vx >= -K) cls = 1;                 // own line, newest K
-        else if (vz == 0 && vy == -1 && vx >= w + 1 - K) cls = 2;    // previous line, newest K
-        meta[t] = (unsigned)(dx + 128) | ((unsigned)(dy + 128) << 8) | ((unsigned)(dz + 128) << 16) | (cls << 24);
+        meta[t] = (unsigned)(dx + 128) | ((unsigned)(dy + 128) << 8) | ((unsigned)(dz + 128) << 16);
     }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < B * SW_D; ++i) mbar_init(&mbar[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    unsigned phase = 0;  // compute warps: expected parity of each ring slot (bit s)
+    int consumed_rows = 0;
+    bool last_ok = true;
     const long long nb = (G.nlines + B - 1) / B;
 
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) sband = atomicAdd(A.counter, 1u);
-        if (threadIdx.x < SW_MAXB) {
-            fin_prog[threadIdx.x] = 0;
-            bulk_prog[threadIdx.x] = 0;
+        if (threadIdx.x == 0) {
+            sband = atomicAdd(A.counter, 1u);
+            s_tick = 0;
+            s_halo = 0;
+            s_abort = (*(volatile int *)A.err != 0) ? 1 : 0;
+            for (int b = 0; b < SW_MAXB; ++b) s_issued[b] = 0;
         }
         __syncthreads();
         const long long band = sband;
         if (band >= nb) return;
-        const long long v = band * B + b;  // virtual line index (sweep order)
-        if (v >= G.nlines) continue;
-        const long long line = DIR > 0 ? v : G.nlines - 1 - v;
-        const int j = (G.d >= 2) ? (int)(line % n1) : 0;
-        const int k = (G.d == 3) ? (int)(line / n1) : 0;
-        const int jv = DIR > 0 ? j : n1 - 1 - j;
-        const int kv = DIR > 0 ? k : n1 - 1 - k;
-        const bool has_prev = (G.d >= 2) && jv >= 1;        // previous line of the same plane
-        const bool prev_in_band = has_prev && b >= 1;
-        const long long prev_real = DIR > 0 ? line - 1 : line + 1;
-        long long vplane = -1;                              // 3D: line (j+w, k-1) in sweep terms
-        if (G.d == 3 && kv >= 1) vplane = (long long)min(jv + w, n1 - 1) + (long long)n1 * (kv - 1);
-        const bool plane_in_band = vplane >= band * B;
-        const long long plane_real = vplane < 0 ? -1 : (DIR > 0 ? vplane : G.nlines - 1 - vplane);
+        const long long v0 = band * B;
+        const int nbl = (int)min((long long)B, G.nlines - v0);
+        const int nt = n1 + (w + 1) * (nbl - 1);
+        // row buffers: rows 0..w-1 hold the halo (virtual lines v0-w..v0-1), rows
+        // w..w+B-1 the band; position q of a row sits at rowoff[row] + q, aligned
+        // like the line in global memory so 16-byte copies land on 16-byte boundaries
+        if (threadIdx.x < w + B) {
+            long long vl = v0 - w + threadIdx.x;
+            int shift = 0;
+            if (vl >= 0 && vl < G.nlines) {
+                long long gl = DIR > 0 ? vl : G.nlines - 1 - vl;
+                shift = (int)((gl * (long long)n1) % CE);
+            }
+            rowoff[threadIdx.x] = threadIdx.x * RS + PADL + shift;
+        }
+        for (int e = threadIdx.x; e < (w + B) * RS; e += blockDim.x) sy[e] = AT(0);
+        const bool aborted = s_abort != 0;
+        if (role < 0 && wid < nbl && !aborted) {
+            const long long line = DIR > 0 ? v0 + wid : G.nlines - 1 - (v0 + wid);
+            for (int q = lane; q < n1; q += 32) srhs[wid * n1 + q] = rhs[q + (long long)n1 * line];
+        }
+        __syncthreads();
 
-        if (is_bulk) {
-            // ------------------------------------------------------------ bulk warp
-            V *myring = ring + (size_t)b * D * RL;
-            double *myrhs = rhsring + b * D;
-            const int nch = RL * (int)sizeof(V) / 16;
-            auto issue = [&](int p) {
-                if (p < n1) {
-                    int ii = DIR > 0 ? p : n1 - 1 - p;
-                    long long r = ii + (long long)n1 * line;
-                    const char *src = (const char *)(F + r * RL);
-                    char *dst = (char *)(myring + (size_t)(p % D) * RL);
-                    for (int c = lane; c < nch; c += 32) cp_async16(dst + 16 * c, src + 16 * c);
-                    if (lane == 0) cp_async8(&myrhs[p % D], &A.rhs[r]);
+        if (role == 0) {
+            // -------------------------------------------------------------- TMA producer
+            // row q of line b goes to ring slot q % D once row q - D (same slot) has
+            // been consumed, i.e. after tick q - D + (w+1) b
+            if (lane == 0 && !aborted) {
+                const unsigned rowbytes = (unsigned)(RL * sizeof(V));
+                int q[SW_MAXB];
+                for (int b = 0; b < SW_MAXB; ++b) q[b] = (b < nbl) ? 0 : n1;
+                const long long t0 = clock64();
+                for (;;) {
+                    const int tk = (int)*(volatile unsigned *)&s_tick;
+                    __threadfence_block();
+                    if (s_abort) break;
+                    bool all = true, any = false;
+                    for (int b = 0; b < nbl; ++b) {
+                        const long long line = DIR > 0 ? v0 + b : G.nlines - 1 - (v0 + b);
+                        while (q[b] < n1 && q[b] - SW_D + 1 + (w + 1) * b <= tk) {
+                            if (!any) fence_proxy_async();
+                            any = true;
+                            const int p = q[b];
+                            const int ii = DIR > 0 ? p : n1 - 1 - p;
+                            uint64_t *bar = &mbar[b * SW_D + p % SW_D];
+                            mbar_expect_tx(bar, rowbytes);
+                            tma_load(ring + ((size_t)b * SW_D + p % SW_D) * RL, F + (ii + (long long)n1 * line) * RL,
+                                     rowbytes, bar);
+                            ++q[b];
+                        }
+                        all = all && q[b] >= n1;
+                    }
+                    if (all) break;
+                    if (!any) {
+                        __nanosleep(32);
+                        if (clock64() - t0 > 4 * kSpinBudgetCycles) {
+                            set_err(A.err, DERR_TIMEOUT);
+                            break;
+                        }
+                    }
+                }
+                for (int b = 0; b < nbl; ++b) s_issued[b] = q[b];
+            }
+        } else if (role == 1) {
+            // -------------------------------------------------------------- halo loader
+            // lane h-1 stages virtual line v0-h: copies every 16-byte chunk whose
+            // positions of that line are finished (progress acquired from global
+            // memory), waits for the copies, then publishes the common ready count
+            const bool hl = lane < w && (v0 - 1 - lane) >= 0 && !aborted;
+            const long long hv = v0 - 1 - lane;
+            const long long hline = hl ? (DIR > 0 ? hv : G.nlines - 1 - hv) : 0;
+            long long hchunk = 0;
+            int hvis = hl ? 0 : n1;
+            if (hl) hchunk = (DIR > 0 ? hline * n1 : hline * n1 + n1 - 1) / CE;
+            AT *hrow = sy + (hl ? rowoff[w - 1 - lane] : 0);
+            const long long lo = hline * n1, hi = lo + n1 - 1;
+            const long long t0 = clock64();
+            bool live = !aborted;
+            while (live) {
+                if (hvis < n1) {
+                    const unsigned P = ld_acquire(A.gprog + hline);
+                    for (;;) {
+                        long long e0 = hchunk * CE, e1 = e0 + CE - 1;
+                        int q_first = (int)(max(e0, lo) - lo), q_last = (int)(min(e1, hi) - lo);
+                        int vend = DIR > 0 ? q_last + 1 : n1 - q_first;
+                        if (vend > (int)P || hvis >= n1) break;
+                        AT *dst = hrow + (int)(e0 - lo);
+                        if (e0 >= lo && e1 <= hi) {
+                            cp_async16(dst, out + e0);
+                        } else {
+                            // a chunk that straddles the line's ends: copy only this line's
+                            // elements, so the padding stays zero (a neighbour's stale value
+                            // could be NaN, and 0 * NaN would poison a dot product)
+                            for (long long e = max(e0, lo); e <= min(e1, hi); ++e) dst[e - e0] = __ldcg(out + e);
+                        }
+                        hvis = vend;
+                        hchunk += DIR;
+                    }
                 }
                 cp_async_commit();
-            };
-            for (int p = 0; p < D - 1; ++p) issue(p);
-            unsigned pub = 0, seen_prev = 0, seen_plane = 0;
-            bool ok = true;
-            for (int p = 0; p < n1; ++p) {
-                issue(p + D - 1);
-                cp_async_wait<D - 1>();
-                __syncwarp();
-                const int i = DIR > 0 ? p : n1 - 1 - p;
+                cp_async_wait<0>();
+                const int ready = __reduce_min_sync(0xffffffffu, (unsigned)hvis);
                 if (lane == 0) {
-                    if (p - SW_R + 1 > 0) ok = ok && spin_smem(&fin_prog[b], (unsigned)(p - SW_R + 1), A.err);
-                    if (p - K > 0) ok = ok && spin_smem(&fin_prog[b], (unsigned)(p - K), A.err);
-                    if (prev_in_band)
-                        ok = ok && spin_smem(&fin_prog[b - 1], (unsigned)min(p + w + 1 - K, n1), A.err);
-                    if (vplane >= 0 && plane_in_band)
-                        ok = ok && spin_smem(&fin_prog[vplane - band * B], (unsigned)min(p + w + 1, n1), A.err);
-                }
-                if (has_prev && !prev_in_band)
-                    ok = ok && wait_flag_cached(A.gprog + prev_real, (unsigned)min(p + w + 1, n1), A.err, &seen_prev);
-                if (vplane >= 0 && !plane_in_band)
-                    ok = ok && wait_flag_cached(A.gprog + plane_real, (unsigned)min(p + w + 1, n1), A.err, &seen_plane);
-                ok = __all_sync(0xffffffffu, ok);
-                if (!ok) break;
-                __threadfence_block();
-                const V *row = myring + (size_t)(p % D) * RL;
-                double acc = 0.0;
-#pragma unroll 4
-                for (int t = lane; t < nslot; t += 32) {
-                    unsigned m = meta[t];
-                    unsigned cls = m >> 24;
-                    if (cls == 1 || (cls == 2 && prev_in_band)) continue;
-                    int dx = (int)(m & 255u) - 128, dy = (int)((m >> 8) & 255u) - 128, dz = (int)((m >> 16) & 255u) - 128;
-                    int ci = i + dx, cj = j + dy, ck = k + dz;
-                    if (ci < 0 || ci >= n1 || cj < 0 || cj >= n1 || ck < 0 || ck >= n1) continue;
-                    long long cl = line + dy + (long long)n1 * dz;
-                    long long vc = DIR > 0 ? cl : G.nlines - 1 - cl;
-                    double yv = (vc >= band * B) ? sy[(vc - band * B) * n1 + ci] : __ldcg(A.out + ci + (long long)n1 * cl);
-                    acc += (double)row[DIR > 0 ? t : 1 + t] * yv;
-                }
-                acc = warp_sum(acc);
-                const int q = p % SW_R;
-                if (lane < 2 * K) {
-                    const int t = lane;
-                    int vx, vy;
-                    if (t < K) {
-                        vx = -(t + 1);
-                        vy = 0;
-                    } else {
-                        vx = w - (t - K);
-                        vy = -1;
-                    }
-                    int pos = p + vx;
-                    double fv = 0.0;
-                    if (pos >= 0 && pos < n1 && (t < K || prev_in_band)) {
-                        int s = slot_index(G, DIR * vx, DIR * vy, 0);
-                        fv = (double)row[DIR > 0 ? s : s - G.Sc];
-                    }
-                    rlate[((size_t)b * SW_R + q) * SW_LATE + t] = fv;
-                }
-                if (lane == 0) {
-                    rbulk[b * SW_R + q] = acc;
-                    rrhs[b * SW_R + q] = myrhs[p % D];
-                    rdiag[b * SW_R + q] = DIR > 0 ? 1.0 : 1.0 / (double)row[0];
-                }
-                __threadfence_block();
-                __syncwarp();
-                if (lane == 0) bulk_prog[b] = (unsigned)(p + 1);
-                // publish finished values of this line to global memory (lane 0
-                // reads the racy progress word once so the branch is warp-uniform)
-                unsigned fin = 0;
-                if (lane == 0) fin = fin_prog[b];
-                fin = __shfl_sync(0xffffffffu, fin, 0);
-                if (fin >= pub + SW_PUB) {
                     __threadfence_block();
-                    for (unsigned pp = pub + lane; pp < fin; pp += 32) {
-                        int ii = DIR > 0 ? (int)pp : n1 - 1 - (int)pp;
-                        A.out[ii + (long long)n1 * line] = sy[(long long)b * n1 + ii];
-                    }
-                    __threadfence();
-                    __syncwarp();
-                    if (lane == 0) st_release(A.gprog + line, fin);
-                    pub = fin;
+                    *(volatile unsigned *)&s_halo = (unsigned)ready;
+                }
+                if (ready >= n1) break;
+                __nanosleep(64);
+                // warp-uniform exits (the loop uses full-warp collectives)
+                if (__any_sync(0xffffffffu, s_abort != 0)) break;
+                if (__any_sync(0xffffffffu, clock64() - t0 > 4 * kSpinBudgetCycles)) {
+                    if (lane == 0) set_err(A.err, DERR_TIMEOUT);
+                    break;
                 }
             }
-            cp_async_wait<0>();
-            __syncwarp();
-            if (ok) {
-                if (lane == 0) ok = spin_smem(&fin_prog[b], (unsigned)n1, A.err);
-                ok = __shfl_sync(0xffffffffu, ok, 0);
+        } else if (role == 2) {
+            // -------------------------------------------------------------- publisher
+            const bool mine = lane < nbl;
+            const long long line = DIR > 0 ? v0 + lane : G.nlines - 1 - (v0 + lane);
+            int pub = 0, rel = 0;
+            bool finished = !mine;
+            const long long t0 = clock64();
+            while (!__all_sync(0xffffffffu, finished)) {
+                const int tk = (int)*(volatile unsigned *)&s_tick;
+                const bool ab = s_abort != 0;
                 __threadfence_block();
-                for (unsigned pp = pub + lane; pp < (unsigned)n1; pp += 32) {
-                    int ii = DIR > 0 ? (int)pp : n1 - 1 - (int)pp;
-                    A.out[ii + (long long)n1 * line] = sy[(long long)b * n1 + ii];
-                }
-            }
-            __threadfence();
-            __syncwarp();
-            // on failure the error word is set; publishing completion lets dependants finish quickly
-            if (lane == 0) st_release(A.gprog + line, (unsigned)n1);
-            if (!ok && lane == 0) bulk_prog[b] = (unsigned)n1;
-        } else {
-            // ------------------------------------------------------------ finaliser warp
-            bool ok = true;
-            double yprev = 0.0;
-            const long long rowb = (long long)b * n1, rowp = (long long)(b - 1) * n1;
-            for (int p = 0; p < n1; ++p) {
-                if (lane == 0) {
-                    const int i = DIR > 0 ? p : n1 - 1 - p;
-                    ok = ok && spin_smem(&bulk_prog[b], (unsigned)(p + 1), A.err);
-                    __threadfence_block();
-                    const int q = p % SW_R;
-                    const volatile double *lf = rlate + ((size_t)b * SW_R + q) * SW_LATE;
-                    double acc = rrhs[b * SW_R + q] - rbulk[b * SW_R + q];
-                    for (int t = 1; t < K; ++t) {
-                        int pos = p - 1 - t;
-                        if (pos >= 0) acc -= lf[t] * sy[rowb + (DIR > 0 ? pos : n1 - 1 - pos)];
-                    }
-                    if (prev_in_band) {
-                        ok = ok && spin_smem(&fin_prog[b - 1], (unsigned)min(p + w, n1), A.err);
-                        __threadfence_block();
-                        for (int t = K + 1; t < 2 * K; ++t) {
-                            int pos = p + w - (t - K);
-                            if (pos >= 0 && pos < n1) acc -= lf[t] * sy[rowp + (DIR > 0 ? pos : n1 - 1 - pos)];
+                if (mine && !finished) {
+                    const int fin = ab ? n1 : max(0, min(tk - (w + 1) * lane, n1));
+                    if (!ab) {
+                        const int row = rowoff[w + lane];
+                        for (; pub < fin; ++pub) {
+                            const int i = DIR > 0 ? pub : n1 - 1 - pub;
+                            out[i + (long long)n1 * line] = sy[row + i];
                         }
-                        ok = ok && spin_smem(&fin_prog[b - 1], (unsigned)min(p + w + 1, n1), A.err);
-                        __threadfence_block();
-                        int pos = p + w;
-                        if (pos < n1) acc -= lf[K] * sy[rowp + (DIR > 0 ? pos : n1 - 1 - pos)];
                     }
-                    if (p >= 1) acc -= lf[0] * yprev;
-                    double val = acc * rdiag[b * SW_R + q];
-                    sy[rowb + i] = val;
-                    yprev = val;
-                    __threadfence_block();
-                    fin_prog[b] = ok ? (unsigned)(p + 1) : (unsigned)n1;
+                    if (fin >= rel + SW_PUB || fin == n1) {
+                        __threadfence();
+                        st_release(A.gprog + line, (unsigned)fin);
+                        rel = fin;
+                        if (fin == n1) finished = true;
+                    }
                 }
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                if (!ok) break;
+                if (!__all_sync(0xffffffffu, finished)) {
+                    __nanosleep(64);
+                    if (clock64() - t0 > 4 * kSpinBudgetCycles) {  // the compute warps' waits are bounded
+                        set_err(A.err, DERR_TIMEOUT);
+                        finished = true;
+                    }
+                }
+            }
+        } else {
+            // -------------------------------------------------------------- compute warp
+            const int b = wid;
+            const bool live = b < nbl;
+            const long long v = v0 + b;
+            const long long line = DIR > 0 ? v : G.nlines - 1 - v;
+            const int j = (G.d >= 2 && live) ? (int)(line % n1) : 0;
+            const int k = (G.d == 3 && live) ? (int)(line / n1) : 0;
+            const int kv = DIR > 0 ? k : n1 - 1 - k;
+            const int jv = DIR > 0 ? j : n1 - 1 - j;
+            long long vplane = -1;
+            if (live && G.d == 3 && kv >= 1) vplane = (long long)min(jv + w, n1 - 1) + (long long)n1 * (kv - 1);
+            const long long plane_real = vplane < 0 ? -1 : (DIR > 0 ? vplane : G.nlines - 1 - vplane);
+            unsigned seen_plane = 0;
+            // register-resident stencil: offset of each of this lane's slots in the row buffers
+            int off[SW_KS];
+#pragma unroll
+            for (int kk = 0; kk < SW_KS; ++kk) {
+                const int t = lane + 32 * kk;
+                off[kk] = 0;
+                if (regpath && t < nslot) {
+                    const unsigned m = meta[t];
+                    const int dx = (int)(m & 255u) - 128, dy = (int)((m >> 8) & 255u) - 128;
+                    off[kk] = rowoff[b + w + DIR * dy] + dx;
+                }
+            }
+            const V *myring = ring + (size_t)b * SW_D * RL;
+            uint64_t *mybar = mbar + b * SW_D;
+            const int myrow = rowoff[b + w];
+            bool ok = !aborted;
+            int tick = 0;
+            for (; tick < nt && ok; ++tick) {
+                const int p = tick - (w + 1) * b;
+                const bool act = live && p >= 0 && p < n1;
+                if (act) {
+                    // halo lines (only bands after the first have any) up to position p + w
+                    if (v0 > 0 && b < w) ok = wait_smem_at_least(&s_halo, (unsigned)min(tick + w + 1, n1), &s_abort, A.err);
+                    const int slot = p % SW_D;
+                    if (ok && !mbar_wait(&mybar[slot], (phase >> slot) & 1u, A.err)) ok = false;
+                    phase ^= 1u << slot;
+                    if (vplane >= 0 && ok)
+                        ok = wait_flag_cached(A.gprog + plane_real, (unsigned)min(p + w + 1, n1), A.err, &seen_plane);
+                    ok = __all_sync(0xffffffffu, ok);
+                    __threadfence_block();
+                }
+                if (act && ok) {
+                    const int i = DIR > 0 ? p : n1 - 1 - p;
+                    const V *row = myring + (size_t)(p % SW_D) * RL + (DIR > 0 ? 0 : 1);
+                    AT acc = 0;
+                    if (regpath) {
+#pragma unroll
+                        for (int kk = 0; kk < SW_KS; ++kk) {
+                            const int t = lane + 32 * kk;
+                            if (t < nslot) acc += (AT)row[t] * sy[off[kk] + i];
+                        }
+                    } else {
+                        for (int t = lane; t < nslot; t += 32) {
+                            const unsigned m = meta[t];
+                            const int dx = (int)(m & 255u) - 128, dy = (int)((m >> 8) & 255u) - 128,
+                                      dz = (int)((m >> 16) & 255u) - 128;
+                            const int ci = i + dx, cj = j + dy, ck = k + dz;
+                            if (ci < 0 || ci >= n1 || cj < 0 || cj >= n1 || ck < 0 || ck >= n1) continue;
+                            AT yv;
+                            if (dz == 0)
+                                yv = sy[rowoff[b + w + DIR * dy] + ci];
+                            else
+                                yv = __ldcg(out + ci + (long long)n1 * (cj + (long long)n1 * ck));
+                            acc += (AT)row[t] * yv;
+                        }
+                    }
+                    acc = warp_sum(acc);
+                    if (lane == 0) {
+                        AT val = srhs[b * n1 + i] - acc;
+                        if (DIR < 0) val = val / (AT)row[-1];
+                        sy[myrow + i] = val;
+                    }
+                }
+                if (!__all_sync(0xffffffffu, ok)) ok = false;
+                if (!ok && lane == 0) s_abort = 1;
+                named_barrier(1, 32 * B);
+                if (s_abort) ok = false;
+                if (b == 0 && lane == 0) {
+                    __threadfence_block();
+                    *(volatile unsigned *)&s_tick = ok ? (unsigned)(tick + 1) : (unsigned)(nt + (w + 1) * B);
+                }
+            }
+            consumed_rows = live ? max(0, min(tick - (w + 1) * b, n1)) : 0;
+            last_ok = ok;
+        }
+        // after an abort, wait (bounded) for factor rows the producer issued but this
+        // warp did not consume, so no bulk copy lands in shared memory after the band
+        __syncthreads();
+        if (role < 0 && !last_ok && wid < nbl) {
+            for (int pp = consumed_rows; pp < s_issued[wid]; ++pp) {
+                const int slot = pp % SW_D;
+                mbar_wait(&mbar[wid * SW_D + slot], (phase >> slot) & 1u, A.err);
+                phase ^= 1u << slot;
             }
         }
     }
 }
 
-template <typename V, int DIR, int D>
+template <typename V, typename AT, int DIR>
 static int launch_sweep(const SweepArgs &A, size_t smem, unsigned grid, cudaStream_t s)
 {
     static size_t attr = 0;  // benign race: setting the attribute twice is harmless
     if (smem > attr) {
-        LSG_CK(cudaFuncSetAttribute(k_sweep<V, DIR, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LSG_CK(cudaFuncSetAttribute(k_sweep<V, AT, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = smem;
     }
     ::lsg::count_launch();
-    k_sweep<V, DIR, D><<<grid, 64 * A.B, smem, s>>>(A);
+    k_sweep<V, AT, DIR><<<grid, 32 * (A.B + SW_HELP), smem, s>>>(A);
     LSG_CK(cudaGetLastError());
     return LSG_OK;
 }
 
-template <typename V>
-static int sweeps(lsg_ctx *c, const double *r, double *z, const int *done, cudaStream_t s)
+template <typename V, typename AT>
+static int sweeps(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done, cudaStream_t s)
 {
     const Geom &g = c->g;
     SweepArgs A;
     A.G = sgeo(g);
     A.done = done;
     A.err = c->err;
-    A.K = std::min(SW_K, g.w);
-    // lines per CTA and ring depth: the largest that fit in shared memory
-    const size_t budget = 200 * 1024;
-    int B = SW_MAXB, D = 4;
-    auto fits = [&](int b, int d, int RL) {
-        return sweep_layout(g.n1, b, d, RL, (int)sizeof(V), g.Sc).total <= budget;
-    };
+    // lines per CTA: the largest that fits the shared-memory budget
+    const size_t budget = 210 * 1024;
     const int RLmax = std::max(g.SL, g.SU);
-    while (B > 1 && !fits(B, D, RLmax)) {
-        if (D == 4)
-            D = 2;
-        else {
-            B /= 2;
-            D = 4;
-        }
-    }
-    if (!fits(B, D, RLmax)) D = 2;
-    if (!fits(B, D, RLmax)) return LSG_ERR_ARG;  // stencil too large for one row in shared memory
+    int B = SW_MAXB;
+    while (B > 1 && sweep_layout(g.n1, g.w, B, RLmax, (int)sizeof(V), g.Sc, (int)sizeof(AT)).total > budget) B /= 2;
+    if (sweep_layout(g.n1, g.w, B, RLmax, (int)sizeof(V), g.Sc, (int)sizeof(AT)).total > budget) return LSG_ERR_ARG;
+    if (g.w > 31) return LSG_ERR_ARG;  // one halo lane per previous line
     if (B > g.nlines) B = (int)std::max<long long>(1, g.nlines);
     A.B = B;
     int dev = 0, nsm = 0;
@@ -375,33 +507,36 @@ static int sweeps(lsg_ctx *c, const double *r, double *z, const int *done, cudaS
     A.F = c->Lv;
     A.RL = g.SL;
     A.rhs = r;
-    A.out = c->ys;
+    A.out = ytmp;
     A.gprog = c->prog;
     A.counter = c->counters + 1;
-    size_t smf = sweep_layout(g.n1, B, D, g.SL, (int)sizeof(V), g.Sc).total;
-    if (D == 4)
-        LSG_TRY((launch_sweep<V, 1, 4>(A, smf, grid, s)));
-    else
-        LSG_TRY((launch_sweep<V, 1, 2>(A, smf, grid, s)));
+    size_t smf = sweep_layout(g.n1, g.w, B, g.SL, (int)sizeof(V), g.Sc, (int)sizeof(AT)).total;
+    LSG_TRY((launch_sweep<V, AT, 1>(A, smf, grid, s)));
     // backward: U z = y
     A.F = c->Uv;
     A.RL = g.SU;
-    A.rhs = c->ys;
+    A.rhs = ytmp;
     A.out = z;
     A.gprog = c->prog + g.nlines;
     A.counter = c->counters + 2;
-    size_t smb = sweep_layout(g.n1, B, D, g.SU, (int)sizeof(V), g.Sc).total;
-    if (D == 4)
-        LSG_TRY((launch_sweep<V, -1, 4>(A, smb, grid, s)));
-    else
-        LSG_TRY((launch_sweep<V, -1, 2>(A, smb, grid, s)));
+    size_t smb = sweep_layout(g.n1, g.w, B, g.SU, (int)sizeof(V), g.Sc, (int)sizeof(AT)).total;
+    LSG_TRY((launch_sweep<V, AT, -1>(A, smb, grid, s)));
     return LSG_OK;
 }
 
+// FP64 vectors: FP64 factors with FP64 accumulation, or (mixed contexts) FP32
+// factors with FP64 accumulation.
 int apply_Minv(lsg_ctx *c, const double *r, double *z, const int *done, cudaStream_t s)
 {
-    if (c->precision == LSG_FP64) return sweeps<double>(c, r, z, done, s);
-    return sweeps<float>(c, r, z, done, s);
+    if (c->precision == LSG_FP64) return sweeps<double, double>(c, r, z, c->ys, done, s);
+    return sweeps<float, double>(c, r, z, c->ys, done, s);
+}
+
+// FP32 vectors (inner solve of the mixed form): FP32 factors, FP32 accumulation.
+int apply_Minv32(lsg_ctx *c, const float *r, float *z, const int *done, cudaStream_t s)
+{
+    if (c->precision == LSG_FP64) return LSG_ERR_ARG;
+    return sweeps<float, float>(c, r, z, c->y32, done, s);
 }
 
 }  // namespace lsg

@@ -180,6 +180,12 @@ __global__ void k_weighted(int d, int Q, long long nq, const double *w, const do
     Wg[g] = W;
 }
 
+__global__ void k_to_float(long long n, const double *a, float *b)
+{
+    long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (g < n) b[g] = (float)a[g];
+}
+
 __global__ void k_any_nonzero(long long n, const double *v, int *flag)
 {
     long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -312,6 +318,13 @@ int build_tables(lsg_ctx *c, const double *a_dev, const double *b_dev, cudaStrea
                                                       c->Wg, c->err);
     LSG_CK(cudaGetLastError());
 
+    if (c->Wa32) {
+        ::lsg::count_launch();
+        k_to_float<<<blocks_for(g.nq, 256), 256, 0, s>>>(g.nq, c->Wa, c->Wa32);
+        ::lsg::count_launch();
+        k_to_float<<<blocks_for(g.nq, 256), 256, 0, s>>>(g.nq, c->Wb, c->Wb32);
+        LSG_CK(cudaGetLastError());
+    }
     // has_b: any nonzero b sample
     int *flag = nullptr;
     LSG_CK(cudaMallocAsync((void **)&flag, sizeof(int), s));

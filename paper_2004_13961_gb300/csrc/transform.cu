@@ -18,23 +18,26 @@
 
 namespace lsg {
 
+template <typename T>
 struct XfTerm {
-    const double *x;
+    const T *x;
     int tab;  // 0: phi (mirror sign +1), 1: phi' (mirror sign -1)
 };
+template <typename T>
 struct XfOut {
-    double *y;
-    const double *scale;  // optional pointwise factor at the output (W a or W b)
+    T *y;
+    const T *scale;  // optional pointwise factor at the output (W a or W b)
     int nterm;
-    XfTerm t[2];
+    XfTerm<T> t[2];
 };
+template <typename T>
 struct XfJob {
     int nout;
-    XfOut o[4];
+    XfOut<T> o[4];
     long long B;     // batch: product of the untouched axes (output row length)
     int Q, Qh, n1, KP;
-    const double *tabE[2], *tabO[2];  // [QhP][KP]
-    const int *done;                  // optional: skip when *done != 0
+    const T *tabE[2], *tabO[2];  // [QhP][KP]
+    const int *done;             // optional: skip when *done != 0
 };
 
 constexpr int XT = 256;  // threads per transform CTA
@@ -43,23 +46,23 @@ constexpr int XT = 256;  // threads per transform CTA
 // axis, length Q).  out[q][b] = sum_k T[q][k] x[b][k] for the term's table T.
 // Tile: TP half-nodes x TB batch columns; 16x16 threads, each RP x RB outputs
 // for the even and the odd half.
-template <int TP, int TB, int TK>
-__global__ void __launch_bounds__(XT) k_xf_fwd(const __grid_constant__ XfJob job)
+template <typename T, int TP, int TB, int TK>
+__global__ void __launch_bounds__(XT) k_xf_fwd(const __grid_constant__ XfJob<T> job)
 {
     if (job.done && *job.done) return;
-    const XfOut &O = job.o[blockIdx.z];
+    const XfOut<T> &O = job.o[blockIdx.z];
     constexpr int RP = TP / 16, RB = TB / 16;
-    __shared__ double sAe[TK][TP + 1], sAo[TK][TP + 1];
-    __shared__ double sXe[TK][TB + 1], sXo[TK][TB + 1];
+    __shared__ T sAe[TK][TP + 1], sAo[TK][TP + 1];
+    __shared__ T sXe[TK][TB + 1], sXo[TK][TB + 1];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int p0 = blockIdx.x * TP;
     const long long b0 = (long long)blockIdx.y * TB;
-    const XfTerm tm = O.t[0];
-    const double *TE = job.tabE[tm.tab], *TO = job.tabO[tm.tab];
+    const XfTerm<T> tm = O.t[0];
+    const T *TE = job.tabE[tm.tab], *TO = job.tabO[tm.tab];
     const int n1 = job.n1, KP = job.KP;
     const long long B = job.B;
 
-    double ae[RP][RB], ao[RP][RB];
+    T ae[RP][RB], ao[RP][RB];
 #pragma unroll
     for (int i = 0; i < RP; ++i)
 #pragma unroll
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(XT) k_xf_fwd(const __grid_constant__ XfJob job
             int aa = idx % (2 * TK), bb = idx / (2 * TK);
             int a = 2 * m0 + aa;
             long long b = b0 + bb;
-            double v = (b < B && a < n1) ? tm.x[b * n1 + a] : 0.0;
+            T v = (b < B && a < n1) ? tm.x[b * n1 + a] : T(0);
             if (aa & 1)
                 sXo[aa >> 1][bb] = v;
             else
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(XT) k_xf_fwd(const __grid_constant__ XfJob job
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < TK; ++kk) {
-            double re[RP], ro[RP], ce[RB], co[RB];
+            T re[RP], ro[RP], ce[RB], co[RB];
 #pragma unroll
             for (int i = 0; i < RP; ++i) {
                 re[i] = sAe[kk][ty + 16 * i];
@@ -109,7 +112,7 @@ __global__ void __launch_bounds__(XT) k_xf_fwd(const __grid_constant__ XfJob job
         }
         __syncthreads();
     }
-    const double sg = tm.tab ? -1.0 : 1.0;
+    const T sg = tm.tab ? T(-1) : T(1);
     const int Q = job.Q, Qh = job.Qh;
 #pragma unroll
     for (int i = 0; i < RP; ++i) {
@@ -120,8 +123,8 @@ __global__ void __launch_bounds__(XT) k_xf_fwd(const __grid_constant__ XfJob job
         for (int j = 0; j < RB; ++j) {
             long long b = b0 + tx + 16 * j;
             if (b >= B) continue;
-            double v1 = ae[i][j] + ao[i][j];
-            double v2 = sg * (ae[i][j] - ao[i][j]);
+            T v1 = ae[i][j] + ao[i][j];
+            T v2 = sg * (ae[i][j] - ao[i][j]);
             if (O.scale) {
                 v1 *= O.scale[(size_t)q1 * B + b];
                 v2 *= O.scale[(size_t)q2 * B + b];
@@ -135,30 +138,30 @@ __global__ void __launch_bounds__(XT) k_xf_fwd(const __grid_constant__ XfJob job
 // Backward: grid values (fastest axis, length Q) -> coefficients (new slowest
 // axis, length n1).  out[k][b] = sum_terms sum_q T[q][k] x[b][q]; the input is
 // folded on load into x[q] + s x[Q-1-q] (even k) and x[q] - s x[Q-1-q] (odd k).
-template <int TM, int TB, int TK>
-__global__ void __launch_bounds__(XT) k_xf_bwd(const __grid_constant__ XfJob job)
+template <typename T, int TM, int TB, int TK>
+__global__ void __launch_bounds__(XT) k_xf_bwd(const __grid_constant__ XfJob<T> job)
 {
     if (job.done && *job.done) return;
-    const XfOut &O = job.o[blockIdx.z];
+    const XfOut<T> &O = job.o[blockIdx.z];
     constexpr int RM = TM / 16, RB = TB / 16;
-    __shared__ double sTe[TK][TM + 1], sTo[TK][TM + 1];
-    __shared__ double sP[TK][TB + 1], sM[TK][TB + 1];
+    __shared__ T sTe[TK][TM + 1], sTo[TK][TM + 1];
+    __shared__ T sP[TK][TB + 1], sM[TK][TB + 1];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int m0 = blockIdx.x * TM;
     const long long b0 = (long long)blockIdx.y * TB;
     const int Q = job.Q, Qh = job.Qh, KP = job.KP;
     const long long B = job.B;
 
-    double ae[RM][RB], ao[RM][RB];
+    T ae[RM][RB], ao[RM][RB];
 #pragma unroll
     for (int i = 0; i < RM; ++i)
 #pragma unroll
         for (int j = 0; j < RB; ++j) ae[i][j] = ao[i][j] = 0.0;
 
     for (int term = 0; term < O.nterm; ++term) {
-        const XfTerm tm = O.t[term];
-        const double *TE = job.tabE[tm.tab], *TO = job.tabO[tm.tab];
-        const double sg = tm.tab ? -1.0 : 1.0;
+        const XfTerm<T> tm = O.t[term];
+        const T *TE = job.tabE[tm.tab], *TO = job.tabO[tm.tab];
+        const T sg = tm.tab ? T(-1) : T(1);
         for (int q0 = 0; q0 < Qh; q0 += TK) {
             for (int idx = tid; idx < TK * TM; idx += XT) {
                 int mm = idx % TM, qq = idx / TM;
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(XT) k_xf_bwd(const __grid_constant__ XfJob job
                 int qq = idx % TK, bb = idx / TK;
                 int q = q0 + qq, q2 = Q - 1 - q;
                 long long b = b0 + bb;
-                double v1 = 0.0, v2 = 0.0;
+                T v1 = 0, v2 = 0;
                 if (q < Qh && b < B) {
                     v1 = tm.x[b * Q + q];
                     if (q2 != q) v2 = tm.x[b * Q + q2];
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(XT) k_xf_bwd(const __grid_constant__ XfJob job
             __syncthreads();
 #pragma unroll
             for (int kk = 0; kk < TK; ++kk) {
-                double re[RM], ro[RM], cp[RB], cm[RB];
+                T re[RM], ro[RM], cp[RB], cm[RB];
 #pragma unroll
                 for (int i = 0; i < RM; ++i) {
                     re[i] = sTe[kk][ty + 16 * i];
@@ -218,7 +221,8 @@ __global__ void __launch_bounds__(XT) k_xf_bwd(const __grid_constant__ XfJob job
     }
 }
 
-static void job_init(XfJob &j, const lsg_ctx *c, long long B, const int *done)
+template <typename T>
+static void job_init_t(XfJob<T> &j, const lsg_ctx *c, const T *tab, long long B, const int *done)
 {
     const Geom &g = c->g;
     j.nout = 0;
@@ -228,45 +232,61 @@ static void job_init(XfJob &j, const lsg_ctx *c, long long B, const int *done)
     j.n1 = g.n1;
     j.KP = g.KP;
     size_t blk = (size_t)g.QhP * g.KP;
-    j.tabE[0] = c->tab;
-    j.tabO[0] = c->tab + blk;
-    j.tabE[1] = c->tab + 2 * blk;
-    j.tabO[1] = c->tab + 3 * blk;
+    j.tabE[0] = tab;
+    j.tabO[0] = tab + blk;
+    j.tabE[1] = tab + 2 * blk;
+    j.tabO[1] = tab + 3 * blk;
     j.done = done;
 }
-static void add_out(XfJob &j, double *y, const double *scale, const double *x0, int t0,
-                    const double *x1 = nullptr, int t1 = 0)
+static void job_init(XfJob<double> &j, const lsg_ctx *c, long long B, const int *done)
 {
-    XfOut &o = j.o[j.nout++];
+    job_init_t<double>(j, c, c->tab, B, done);
+}
+static void job_init(XfJob<float> &j, const lsg_ctx *c, long long B, const int *done)
+{
+    job_init_t<float>(j, c, c->tab32, B, done);
+}
+template <typename T>
+struct ident {
+    using type = T;
+};
+template <typename T>
+static void add_out(XfJob<T> &j, typename ident<T>::type *y, const typename ident<T>::type *scale,
+                    const typename ident<T>::type *x0, int t0, const typename ident<T>::type *x1 = nullptr,
+                    int t1 = 0)
+{
+    XfOut<T> &o = j.o[j.nout++];
     o.y = y;
     o.scale = scale;
     o.nterm = x1 ? 2 : 1;
-    o.t[0] = XfTerm{x0, t0};
-    o.t[1] = XfTerm{x1, t1};
+    o.t[0] = XfTerm<T>{x0, t0};
+    o.t[1] = XfTerm<T>{x1, t1};
 }
 
-static int launch_fwd(const XfJob &j, cudaStream_t s)
+template <typename T>
+static int launch_fwd(const XfJob<T> &j, cudaStream_t s)
 {
     constexpr int TP = 32, TB = 64, TK = 16;
     dim3 grid((j.Qh + TP - 1) / TP, (unsigned)((j.B + TB - 1) / TB), j.nout);
     ::lsg::count_launch();
-    k_xf_fwd<TP, TB, TK><<<grid, XT, 0, s>>>(j);
+    k_xf_fwd<T, TP, TB, TK><<<grid, XT, 0, s>>>(j);
     LSG_CK(cudaGetLastError());
     return LSG_OK;
 }
-static int launch_bwd(const XfJob &j, cudaStream_t s)
+template <typename T>
+static int launch_bwd(const XfJob<T> &j, cudaStream_t s)
 {
     int ne = (j.n1 + 1) / 2;
     if (j.B >= 2048) {
         constexpr int TM = 32, TB = 64, TK = 16;
         dim3 grid((ne + TM - 1) / TM, (unsigned)((j.B + TB - 1) / TB), j.nout);
         ::lsg::count_launch();
-        k_xf_bwd<TM, TB, TK><<<grid, XT, 0, s>>>(j);
+        k_xf_bwd<T, TM, TB, TK><<<grid, XT, 0, s>>>(j);
     } else {
         constexpr int TM = 32, TB = 32, TK = 16;
         dim3 grid((ne + TM - 1) / TM, (unsigned)((j.B + TB - 1) / TB), j.nout);
         ::lsg::count_launch();
-        k_xf_bwd<TM, TB, TK><<<grid, XT, 0, s>>>(j);
+        k_xf_bwd<T, TM, TB, TK><<<grid, XT, 0, s>>>(j);
     }
     LSG_CK(cudaGetLastError());
     return LSG_OK;
@@ -282,34 +302,35 @@ size_t workspace_elems(const Geom &g)
 
 // y = K x (Sec. 4.3), every stage on the device.  `done` (optional) makes every
 // kernel a no-op once a device-side PCG has converged.
-int apply_K(lsg_ctx *c, const double *x, double *y, const int *done, cudaStream_t s)
+template <typename T>
+static int apply_K_t(lsg_ctx *c, const T *x, T *y, const int *done, T *ws, const T *Wa, const T *Wb,
+                     cudaStream_t s)
 {
     const Geom &g = c->g;
     const long long Q = g.Q, n1 = g.n1;
-    double *ws = c->ws;
-    XfJob j;
+    XfJob<T> j;
     if (g.d == 1) {
-        double *H = ws, *Gx = ws + Q;
+        T *H = ws, *Gx = ws + Q;
         job_init(j, c, 1, done);
-        add_out(j, H, c->Wb, x, 0);
-        add_out(j, Gx, c->Wa, x, 1);
+        add_out(j, H, Wb, x, 0);
+        add_out(j, Gx, Wa, x, 1);
         LSG_TRY(launch_fwd(j, s));
         job_init(j, c, 1, done);
         add_out(j, y, nullptr, H, 0, Gx, 1);
         return launch_bwd(j, s);
     }
     if (g.d == 2) {
-        double *AP = ws, *AD = ws + Q * n1;           // [Q][n1]
-        double *H = ws + 2 * Q * n1, *Gy = H + Q * Q, *Gx = Gy + Q * Q;  // [Q][Q]
-        double *P1 = AP, *P2 = AD;                    // [n1][Q] (reuse)
+        T *AP = ws, *AD = ws + Q * n1;           // [Q][n1]
+        T *H = ws + 2 * Q * n1, *Gy = H + Q * Q, *Gx = Gy + Q * Q;  // [Q][Q]
+        T *P1 = AP, *P2 = AD;                    // [n1][Q] (reuse)
         job_init(j, c, n1, done);                     // contract x: U[j][k]
         add_out(j, AP, nullptr, x, 0);
         add_out(j, AD, nullptr, x, 1);
         LSG_TRY(launch_fwd(j, s));
         job_init(j, c, Q, done);                      // contract y: A[q][j]
-        add_out(j, H, c->Wb, AP, 0);
-        add_out(j, Gy, c->Wa, AP, 1);
-        add_out(j, Gx, c->Wa, AD, 0);
+        add_out(j, H, Wb, AP, 0);
+        add_out(j, Gy, Wa, AP, 1);
+        add_out(j, Gx, Wa, AD, 0);
         LSG_TRY(launch_fwd(j, s));
         job_init(j, c, Q, done);                      // contract x-nodes: [r][q]
         add_out(j, P1, nullptr, H, 0, Gx, 1);
@@ -320,10 +341,10 @@ int apply_K(lsg_ctx *c, const double *x, double *y, const int *done, cudaStream_
         return launch_bwd(j, s);
     }
     // d == 3
-    double *A0 = ws, *A1 = ws + Q * n1 * n1;                       // [Q][n1][n1]
-    double *B0 = ws + 2 * Q * n1 * n1, *B1 = B0 + Q * Q * n1, *B2 = B1 + Q * Q * n1;  // [Q][Q][n1]
-    double *F0 = B2 + Q * Q * n1, *F1 = F0 + Q * Q * Q, *F2 = F1 + Q * Q * Q, *F3 = F2 + Q * Q * Q;
-    double *H = F0, *Gz = F1, *Gy = F2, *Gx = F3;
+    T *A0 = ws, *A1 = ws + Q * n1 * n1;                       // [Q][n1][n1]
+    T *B0 = ws + 2 * Q * n1 * n1, *B1 = B0 + Q * Q * n1, *B2 = B1 + Q * Q * n1;  // [Q][Q][n1]
+    T *F0 = B2 + Q * Q * n1, *F1 = F0 + Q * Q * Q, *F2 = F1 + Q * Q * Q, *F3 = F2 + Q * Q * Q;
+    T *H = F0, *Gz = F1, *Gy = F2, *Gx = F3;
     job_init(j, c, n1 * n1, done);                 // x: U[l][j][k] -> [q][l][j]
     add_out(j, A0, nullptr, x, 0);
     add_out(j, A1, nullptr, x, 1);
@@ -334,18 +355,18 @@ int apply_K(lsg_ctx *c, const double *x, double *y, const int *done, cudaStream_
     add_out(j, B2, nullptr, A1, 0);                // phi'_x phi_y
     LSG_TRY(launch_fwd(j, s));
     job_init(j, c, Q * Q, done);                   // z: [r][q][l] -> [s][r][q]
-    add_out(j, H, c->Wb, B0, 0);
-    add_out(j, Gz, c->Wa, B0, 1);
-    add_out(j, Gy, c->Wa, B1, 0);
-    add_out(j, Gx, c->Wa, B2, 0);
+    add_out(j, H, Wb, B0, 0);
+    add_out(j, Gz, Wa, B0, 1);
+    add_out(j, Gy, Wa, B1, 0);
+    add_out(j, Gx, Wa, B2, 0);
     LSG_TRY(launch_fwd(j, s));
-    double *Pa = B0, *Pb = B1, *Pc = B2;           // [n1][Q][Q] = [m][s][r]
+    T *Pa = B0, *Pb = B1, *Pc = B2;           // [n1][Q][Q] = [m][s][r]
     job_init(j, c, Q * Q, done);
     add_out(j, Pa, nullptr, H, 0, Gx, 1);
     add_out(j, Pb, nullptr, Gy, 0);
     add_out(j, Pc, nullptr, Gz, 0);
     LSG_TRY(launch_bwd(j, s));
-    double *Ra = A0, *Rc = A1;                     // [n1][n1][Q] = [n'][m][s]
+    T *Ra = A0, *Rc = A1;                     // [n1][n1][Q] = [n'][m][s]
     job_init(j, c, n1 * Q, done);
     add_out(j, Ra, nullptr, Pa, 0, Pb, 1);
     add_out(j, Rc, nullptr, Pc, 0);
@@ -353,6 +374,16 @@ int apply_K(lsg_ctx *c, const double *x, double *y, const int *done, cudaStream_
     job_init(j, c, n1 * n1, done);                 // [l'][n'][m]
     add_out(j, y, nullptr, Ra, 0, Rc, 1);
     return launch_bwd(j, s);
+}
+
+int apply_K(lsg_ctx *c, const double *x, double *y, const int *done, cudaStream_t s)
+{
+    return apply_K_t<double>(c, x, y, done, c->ws, c->Wa, c->Wb, s);
+}
+
+int apply_K32(lsg_ctx *c, const float *x, float *y, const int *done, cudaStream_t s)
+{
+    return apply_K_t<float>(c, x, y, done, c->ws32, c->Wa32, c->Wb32, s);
 }
 
 __global__ void k_mul(long long n, const double *a, const double *b, double *out)
@@ -371,7 +402,7 @@ int load_vector(lsg_ctx *c, const double *f, double *F, cudaStream_t s)
     ::lsg::count_launch();
     k_mul<<<(unsigned)((g.nq + 255) / 256), 256, 0, s>>>(g.nq, c->Wg, f, G);
     LSG_CK(cudaGetLastError());
-    XfJob j;
+    XfJob<double> j;
     if (g.d == 1) {
         job_init(j, c, 1, nullptr);
         add_out(j, F, nullptr, G, 0);
@@ -404,7 +435,7 @@ int eval_grid(lsg_ctx *c, const double *u, double *vals, cudaStream_t s)
     const Geom &g = c->g;
     const long long Q = g.Q, n1 = g.n1;
     double *ws = c->ws;
-    XfJob j;
+    XfJob<double> j;
     if (g.d == 1) {
         job_init(j, c, 1, nullptr);
         add_out(j, vals, nullptr, u, 0);
