@@ -216,15 +216,25 @@ def run_native(args, world, rank, local):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2 (129 MB)
 
     last = {}
+    prof = dict(sweep_us=0.0, sweep_calls=0, sweep_l_calls=0, kx_us=0.0, kx_calls=0, ilu_us=0.0, asm_us=0.0)
 
-    def step():
-        ctx = lsg.Context(d, N, T, a, b, Q=Q)
+    def step(timed=False):
+        # the context records CUDA events on its stream around every sweep and K x kernel
+        ctx = lsg.Context(d, N, T, a, b, Q=Q, profile=True)
         ctx.load_vector(f, F)
         u.zero_()
         _, info = ctx.pcg_solve(F, u, rtol=RTOL)
         last["info"] = info
         last["ilu_ms"] = ctx.query(lsg.Q_ILU_US) / 1e3
         last["asm_ms"] = ctx.query(lsg.Q_ASSEMBLE_US) / 1e3
+        if timed:
+            prof["sweep_us"] += ctx.query(lsg.Q_SWEEP_L_US) + ctx.query(lsg.Q_SWEEP_U_US)
+            prof["sweep_calls"] += ctx.query(lsg.Q_SWEEP_L_CALLS) + ctx.query(lsg.Q_SWEEP_U_CALLS)
+            prof["sweep_l_calls"] += ctx.query(lsg.Q_SWEEP_L_CALLS)
+            prof["kx_us"] += ctx.query(lsg.Q_KX_US)
+            prof["kx_calls"] += ctx.query(lsg.Q_KX_CALLS)
+            prof["ilu_us"] += ctx.query(lsg.Q_ILU_US)
+            prof["asm_us"] += ctx.query(lsg.Q_ASSEMBLE_US)
         ctx.close()
 
     for _ in range(args.warmup):
@@ -240,7 +250,7 @@ def run_native(args, world, rank, local):
     for k in range(args.steps):
         flush.fill_(float(k))  # evict L2 between timed steps (outside the events)
         ev[k][0].record()
-        step()
+        step(timed=True)
         ev[k][1].record()
     torch.cuda.synchronize()
     launches = lsg.kernel_launches() - l0
@@ -271,35 +281,76 @@ def run_native(args, world, rank, local):
 
     t_kx = evtime(lambda: ctx.apply_A(x, y), 20)
     t_minv = evtime(lambda: ctx.apply_Minv(F, z), 3)
+    nnz = ctx.query(lsg.Q_NNZ)
     ctx.close()
     hbm, bf16, psrc = peaks()
-    Qh = (Q + 1) // 2
     n1 = N - 1
-    # algorithmic work, parity-folded transforms (4 contractions of half length):
-    # 2D: (8 n1^2 Q + 12 Q^2 n1) / 2 flops
+    # algorithmic work (per launch): a sweep reads its triangle of M's structural
+    # nonzeros (forward: strictly lower, backward: diagonal and upper) plus the
+    # right-hand side and writes its result, all FP64; a K x does the parity-folded
+    # 2D contractions (8 n1^2 Q + 12 Q^2 n1) / 2 flops
+    sweep_bytes_total = 8.0 * (prof["sweep_l_calls"] * ((nnz - n) / 2 + 2 * n)
+                               + (prof["sweep_calls"] - prof["sweep_l_calls"]) * ((nnz + n) / 2 + 2 * n))
     kx_flops = (8.0 * n1 * n1 * Q + 12.0 * Q * Q * n1) / 2.0
-    w = T + 2
-    lower = ((2 * w + 1) ** 2 - 1) // 2
-    sweep_bytes = n * lower * 8 + 3 * n * 8  # factors of one triangle + rhs, out, neighbour reads
-    iters = info["iters"]
-    per_solve = dict(setup_ilu_ms=last["ilu_ms"], setup_assemble_ms=last["asm_ms"],
-                     pcg_kx_ms=iters * t_kx, pcg_minv_ms=iters * t_minv)
-    dominant = max(per_solve, key=per_solve.get)
-    if dominant == "pcg_minv_ms":
-        dur = t_minv / 2.0
-        roof = dict(kernel="k_sweep (one triangular sweep, Alg. 3/4)", bound="hbm", achieved=sweep_bytes / dur / 1e6,
-                    peak=hbm, unit="GB/s", traffic=None)
-    elif dominant == "pcg_kx_ms":
-        dur = t_kx / 4.0
-        roof = dict(kernel="k_xf_fwd/k_xf_bwd (one of 4 FP64 contractions)", bound="alu",
-                    achieved=kx_flops / 4 / dur / 1e9, peak=FP64_PEAK_TFLOPS * 1e3, unit="GFLOP/s", traffic=None)
+    stage_ms = dict(sweeps=prof["sweep_us"] / 1e3, kx=prof["kx_us"] / 1e3, ilu=prof["ilu_us"] / 1e3,
+                    assemble=prof["asm_us"] / 1e3)
+    dominant = max(stage_ms, key=stage_ms.get)
+    if dominant == "sweeps":
+        dur_s = prof["sweep_us"] / 1e6 / max(1, prof["sweep_calls"])
+        roof = dict(kernel="k_sweep (one triangular sweep, Algorithm 3 or 4)", bound="hbm",
+                    achieved=sweep_bytes_total / max(1, prof["sweep_calls"]) / dur_s / 1e9, peak=hbm, unit="GB/s",
+                    launches=prof["sweep_calls"], avg_launch_ms=dur_s * 1e3, traffic=None)
+    elif dominant == "kx":
+        dur_s = prof["kx_us"] / 1e6 / max(1, prof["kx_calls"])
+        roof = dict(kernel="K x (k_xf_fwd + k_xf_bwd, FP64)", bound="alu", achieved=kx_flops / dur_s / 1e12,
+                    peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", launches=prof["kx_calls"], avg_launch_ms=dur_s * 1e3,
+                    traffic=None)
     else:
-        dur = last["ilu_ms"]
-        roof = dict(kernel="k_ilu0 (Alg. 2)", bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS * 1e3,
-                    unit="GFLOP/s", traffic=None)
+        roof = dict(kernel="k_ilu0 (Algorithm 2)", bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS,
+                    unit="TFLOP/s", traffic=None)
     if roof["achieved"] is not None:
         roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["peak_source"] = psrc if roof["bound"] == "hbm" else "measured FP64 FMA loop"
+    roof["peak_source"] = ("of measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if psrc == "measured"
+                           else "of fallback") if roof["bound"] == "hbm" else "of measured FP64 FMA loop"
+    roof["timing"] = "CUDA events on the launching stream around every launch of the timed steps"
+    iters = info["iters"]
+    per_solve = {k + "_ms": v / args.steps for k, v in stage_ms.items()}
+
+    # ---- mixed precision: inner FP32 PCG (FP32 ILU factors, FP32 transforms) in FP64 refinement ----
+    mixed = {}
+    if not args.no_mixed:
+        u64 = u.clone()
+        for name, prec in (("tf32", lsg.MIXED_TF32), ("bf16", lsg.MIXED_BF16)):
+            um = torch.empty_like(u)
+            res = {}
+
+            def mstep():
+                c3 = lsg.Context(d, N, T, a, b, Q=Q, precision=prec)
+                c3.load_vector(f, F)
+                um.zero_()
+                _, inf = c3.pcg_solve(F, um, rtol=1e-10)
+                res["info"] = inf
+                c3.close()
+
+            for _ in range(2):
+                mstep()
+            torch.cuda.synchronize()
+            ms = []
+            for k in range(max(1, min(args.steps, 3))):
+                flush.fill_(float(k))
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record()
+                mstep()
+                s1.record()
+                torch.cuda.synchronize()
+                ms.append(s0.elapsed_time(s1))
+            inf = res["info"]
+            err = float(torch.linalg.norm(um - u64) / torch.linalg.norm(u64))
+            mixed[name] = dict(solves_s=world * 1e3 / max_over_ranks(float(np.mean(ms)), world),
+                               ms_per_solve=float(np.mean(ms)), rtol=1e-10, relres_true=inf["relres_true"],
+                               inner_iters=inf["iters"], refinements=inf["outer_iters"],
+                               rel_err_vs_fp64_gpu=err,
+                               transforms="FP32 CUDA cores (tensor-core transforms not wired yet)")
 
     # ---- e2e: host buffers through the C ABI, copies inside the timed region ----
     ha, hb, hf = p["a"].copy(), p["b"].copy(), p["f"].copy()
@@ -335,7 +386,7 @@ def run_native(args, world, rank, local):
             config=dict(workload=WORKLOAD, l2="256 MB buffer written between timed steps (factors 0.94 GB > L2)",
                         parallelism=f"replicas x{world}"),
             kx_gdof_s=n / (t_kx * 1e-3) / 1e9, kx_ms=t_kx, minv_ms=t_minv, pcg_iters=iters,
-            relres_true=info["relres_true"], breakdown_ms=per_solve,
+            relres_true=info["relres_true"], breakdown_ms_per_solve=per_solve, mixed=mixed or None,
             roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clocks)
         print(json.dumps(line), flush=True)
 
@@ -347,6 +398,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":

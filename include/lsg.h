@@ -68,6 +68,10 @@ enum lsg_precision {
 
 /* lsg_setup_ex flags */
 #define LSG_SETUP_KEEP_M 1u /* keep an unfactored copy of M for lsg_export(LSG_EXPORT_M) */
+#define LSG_SETUP_PROFILE 2u /* time every triangular-sweep kernel and every K x product that
+                                lsg_pcg_solve launches, with CUDA events recorded on the solve's
+                                stream (no extra synchronisation); read with the LSG_Q_SWEEP_* and
+                                LSG_Q_KX_* queries after the solve returns */
 
 /* lsg_export items (host output; sizes from lsg_export_count) */
 enum lsg_export_item {
@@ -92,7 +96,17 @@ enum lsg_query_item {
     LSG_Q_NNZ = 6,          /* structural nonzeros of M */
     LSG_Q_PRECISION = 7,
     LSG_Q_ASSEMBLE_US = 8,  /* setup: M assembly and ordering time, microseconds (CUDA events) */
-    LSG_Q_ILU_US = 9        /* setup: ILU(0) factorisation time, microseconds (CUDA events) */
+    LSG_Q_ILU_US = 9,       /* setup: ILU(0) factorisation time, microseconds (CUDA events) */
+    /* last lsg_pcg_solve of a context set up with LSG_SETUP_PROFILE (-1 without it): summed
+       kernel time in microseconds and launch count of each stage */
+    LSG_Q_SWEEP_L_US = 10,    /* forward sweeps L y = r (Algorithm 3) */
+    LSG_Q_SWEEP_L_CALLS = 11,
+    LSG_Q_SWEEP_U_US = 12,    /* backward sweeps U z = y (Algorithm 4) */
+    LSG_Q_SWEEP_U_CALLS = 13,
+    LSG_Q_KX_US = 14,         /* FP64 matrix-free products inside the PCG loop */
+    LSG_Q_KX_CALLS = 15,
+    LSG_Q_KX_LO_US = 16,      /* low-precision products of the mixed form's inner PCG */
+    LSG_Q_KX_LO_CALLS = 17
 };
 
 typedef struct {

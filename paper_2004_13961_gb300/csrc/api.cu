@@ -152,6 +152,7 @@ static void free_ctx(lsg_ctx *c)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->st_host) cudaFreeHost(c->st_host);
+    prof_destroy(c);
     delete c;
 }
 
@@ -246,6 +247,7 @@ int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, con
     c->g = make_geom(d, N, T, Q);
     c->precision = precision;
     c->flags = flags;
+    if (flags & LSG_SETUP_PROFILE) prof_create(c);
     LSG_CK(cudaGetDevice(&c->device));
     {
         // keep freed context memory in the stream-ordered pool for the next setup
@@ -430,8 +432,13 @@ int lsg_pcg_solve(lsg_ctx *c, const double *F, double *u, double rtol, int kmax,
         du = c->xs;
         LSG_CK(cudaMemcpyAsync(du, u, sizeof(double) * (size_t)c->g.n, cudaMemcpyHostToDevice, s));
     }
+    prof_reset(c);
     int st = (c->precision == LSG_FP64) ? pcg_fp64(c, dF, du, rtol, kmax, info, s)
                                         : pcg_mixed(c, dF, du, rtol, kmax, info, s);
+    if (st == LSG_OK || st == LSG_ERR_NOT_CONVERGED) {
+        int pst = prof_collect(c);
+        if (pst != LSG_OK) st = pst;
+    }
     if (hu) {
         LSG_CK(cudaMemcpyAsync(u, du, sizeof(double) * (size_t)c->g.n, cudaMemcpyDeviceToHost, s));
         LSG_CK(cudaStreamSynchronize(s));
@@ -524,6 +531,14 @@ long long lsg_query(lsg_ctx *c, int item)
     case LSG_Q_PRECISION: return c->precision;
     case LSG_Q_ASSEMBLE_US: return (long long)(c->t_assemble_ms * 1000.0f);
     case LSG_Q_ILU_US: return (long long)(c->t_ilu_ms * 1000.0f);
+    case LSG_Q_SWEEP_L_US: return prof_query(c, PROF_SWEEP_L, false);
+    case LSG_Q_SWEEP_L_CALLS: return prof_query(c, PROF_SWEEP_L, true);
+    case LSG_Q_SWEEP_U_US: return prof_query(c, PROF_SWEEP_U, false);
+    case LSG_Q_SWEEP_U_CALLS: return prof_query(c, PROF_SWEEP_U, true);
+    case LSG_Q_KX_US: return prof_query(c, PROF_KX, false);
+    case LSG_Q_KX_CALLS: return prof_query(c, PROF_KX, true);
+    case LSG_Q_KX_LO_US: return prof_query(c, PROF_KX_LO, false);
+    case LSG_Q_KX_LO_CALLS: return prof_query(c, PROF_KX_LO, true);
     default: return -1;
     }
 }

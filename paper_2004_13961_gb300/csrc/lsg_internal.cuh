@@ -58,6 +58,10 @@ struct PcgState {
     int pad[4];
 };
 
+// stages timed by the optional per-context profiler (LSG_SETUP_PROFILE)
+enum ProfStage : int { PROF_SWEEP_L = 0, PROF_SWEEP_U = 1, PROF_KX = 2, PROF_KX_LO = 3, PROF_STAGES = 4 };
+struct Prof;
+
 // reduction scratch: fixed grid so that sums are deterministic
 constexpr int kRedBlocks = 296;   // 2 x 148..152 SMs, fixed for determinism
 constexpr int kRedThreads = 256;
@@ -106,6 +110,7 @@ struct lsg_ctx {
 
     // setup stage times (milliseconds, CUDA events): tables, assembly, ILU(0)
     float t_tables_ms, t_assemble_ms, t_ilu_ms;
+    lsg::Prof *prof;           // solve-stage event timing (null unless LSG_SETUP_PROFILE)
 };
 
 namespace lsg {
@@ -148,6 +153,15 @@ long long structural_nnz(const Geom &g);
 
 // host-side count of kernel launches issued by the library (all contexts)
 void count_launch();
+
+// optional stage timing (no-ops when the context was set up without LSG_SETUP_PROFILE)
+void prof_create(lsg_ctx *c);
+void prof_destroy(lsg_ctx *c);
+void prof_reset(lsg_ctx *c);
+int prof_begin(lsg_ctx *c, int stage, cudaStream_t s, int *slot);
+int prof_end(lsg_ctx *c, int slot, cudaStream_t s);
+int prof_collect(lsg_ctx *c);
+long long prof_query(const lsg_ctx *c, int stage, bool calls);
 
 // ---------------------------------------------------------------------------
 // device helpers

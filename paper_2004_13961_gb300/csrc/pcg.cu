@@ -204,7 +204,10 @@ static int iteration(lsg_ctx *c, double *x, cudaStream_t s)
     k_rz<<<kRedBlocks, kRedThreads, 0, s>>>(n, c->r, c->z, c->red, cnt, c->st);
     ::lsg::count_launch();
     k_pupd<<<kRedBlocks, kRedThreads, 0, s>>>(n, c->z, c->p, c->st);
+    int slot;
+    LSG_TRY(prof_begin(c, PROF_KX, s, &slot));
     LSG_TRY(apply_K(c, c->p, c->wv, done, s));
+    LSG_TRY(prof_end(c, slot, s));
     ::lsg::count_launch();
     k_pw<<<kRedBlocks, kRedThreads, 0, s>>>(n, c->p, c->wv, c->red, cnt, c->st);
     ::lsg::count_launch();
@@ -476,7 +479,10 @@ static int iteration32(lsg_ctx *c, cudaStream_t s)
     k_rz32<<<kRedBlocks, kRedThreads, 0, s>>>(n, c->r32, c->z32, c->red, cnt, c->st);
     ::lsg::count_launch();
     k_pupd32<<<kRedBlocks, kRedThreads, 0, s>>>(n, c->z32, c->p32, c->st);
+    int slot;
+    LSG_TRY(prof_begin(c, PROF_KX_LO, s, &slot));
     LSG_TRY(apply_K32(c, c->p32, c->w32, done, s));
+    LSG_TRY(prof_end(c, slot, s));
     ::lsg::count_launch();
     k_pw32<<<kRedBlocks, kRedThreads, 0, s>>>(n, c->p32, c->w32, c->red, cnt, c->st);
     ::lsg::count_launch();

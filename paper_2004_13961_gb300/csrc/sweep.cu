@@ -511,7 +511,10 @@ static int sweeps(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done, cud
     A.gprog = c->prog;
     A.counter = c->counters + 1;
     size_t smf = sweep_layout(g.n1, g.w, B, g.SL, (int)sizeof(V), g.Sc, (int)sizeof(AT)).total;
+    int slot;
+    LSG_TRY(prof_begin(c, PROF_SWEEP_L, s, &slot));
     LSG_TRY((launch_sweep<V, AT, 1>(A, smf, grid, s)));
+    LSG_TRY(prof_end(c, slot, s));
     // backward: U z = y
     A.F = c->Uv;
     A.RL = g.SU;
@@ -520,7 +523,9 @@ static int sweeps(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done, cud
     A.gprog = c->prog + g.nlines;
     A.counter = c->counters + 2;
     size_t smb = sweep_layout(g.n1, g.w, B, g.SU, (int)sizeof(V), g.Sc, (int)sizeof(AT)).total;
+    LSG_TRY(prof_begin(c, PROF_SWEEP_U, s, &slot));
     LSG_TRY((launch_sweep<V, AT, -1>(A, smb, grid, s)));
+    LSG_TRY(prof_end(c, slot, s));
     return LSG_OK;
 }
 

@@ -21,12 +21,15 @@ from . import build as _build
 
 FP64, MIXED_TF32, MIXED_BF16 = 0, 1, 2
 SETUP_KEEP_M = 1
+SETUP_PROFILE = 2
 
 EXPORT_GAUSS_X, EXPORT_GAUSS_W, EXPORT_AHAT, EXPORT_BHAT = 0, 1, 2, 3
 EXPORT_BAND_S, EXPORT_BAND_M, EXPORT_M, EXPORT_LU = 4, 5, 6, 7
 
 Q_UNKNOWNS, Q_GRID, Q_HALF_WIDTH, Q_SLOTS, Q_LEVELS, Q_DEVICE_BYTES, Q_NNZ, Q_PRECISION, Q_ASSEMBLE_US, Q_ILU_US = \
     range(10)
+(Q_SWEEP_L_US, Q_SWEEP_L_CALLS, Q_SWEEP_U_US, Q_SWEEP_U_CALLS, Q_KX_US, Q_KX_CALLS, Q_KX_LO_US,
+ Q_KX_LO_CALLS) = range(10, 18)
 
 OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_ILU_BREAKDOWN, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_NONFINITE = \
     0, -1, -2, -3, -4, -5, -6, -7
@@ -186,7 +189,8 @@ def footprint_bytes(d, N, T, Q=0, precision=FP64) -> int:
 class Context:
     """An lsg_ctx: tables, coefficient samples, M's ILU(0) factors and workspaces."""
 
-    def __init__(self, d, N, T, a, b, Q=None, precision=FP64, keep_M=False, stream=None, allow_breakdown=False):
+    def __init__(self, d, N, T, a, b, Q=None, precision=FP64, keep_M=False, stream=None, allow_breakdown=False,
+                 profile=False):
         L = load()
         self._L = L
         self.d, self.N, self.T = d, N, T
@@ -194,7 +198,8 @@ class Context:
         self.precision = precision
         h = ctypes.c_void_p(0)
         st = L.lsg_setup_ex(ctypes.byref(h), d, N, T, self.Q, _ptr(a), _ptr(b), precision,
-                            SETUP_KEEP_M if keep_M else 0, _stream(stream))
+                            (SETUP_KEEP_M if keep_M else 0) | (SETUP_PROFILE if profile else 0),
+                            _stream(stream))
         self.status = st
         self._h = h
         if st != OK and not (allow_breakdown and st == ERR_ILU_BREAKDOWN and h.value):
