@@ -151,80 +151,216 @@ __global__ void k_level_scatter(StencilGeo G, int *cursor, int *order)
 
 // ILU(0), Algorithm 2 in IKJ form on the stencil: for each lower slot k of row
 // r in ascending column order, H(r,k) /= U(k,k), then H(r,j) -= H(r,k) U(k,j)
-// for every upper slot j of row k whose column is in row r's pattern.  One warp
-// per row; rows are claimed in wavefront order, so every row a warp waits for
-// was claimed earlier by a running warp.  A row waits for a dependency line
-// only when its first entry from that line is due (the wait is on the last
-// row it needs from the line, which implies the earlier ones).
+// for every upper slot j of row k whose column is in row r's pattern.
+//
+// One warp per row, rows claimed in wavefront order (a warp only waits for
+// rows claimed earlier by running warps).  The row lives in shared memory for
+// the whole elimination; the U rows it needs are streamed into a per-warp ring
+// of D shared-memory buffers with 16-byte cp.async copies issued D steps
+// ahead, so a step is: one multiply by the stored reciprocal pivot and one
+// masked vector update, all in shared memory.  In stencil slot numbering the
+// target of U(k, slot Sc+u) is simply slot s+u of row r (s: the step's lower
+// slot), valid when the target offset stays in the box and in the pattern;
+// columns outside the grid hold exact zeros in both rows, so they need no
+// test.  Before the first U row of a line is fetched, the warp checks the
+// completion flags of every row it will use from that line (one per lane).
+// A finished row stores 1 / U(r,r) in the pad slot SU-1 of its U row.
+constexpr int ILU_MAX_WARPS = 8;
+
+struct IluSmem {
+    size_t meta, smask, warps, per_warp, total;
+};
+__host__ __device__ inline size_t al16(size_t b) { return (b + 15) / 16 * 16; }
+__host__ __device__ inline IluSmem ilu_layout(int S, int Sc, int SU, int D, int vsize, int nw)
+{
+    IluSmem L;
+    L.meta = 0;
+    L.smask = al16((size_t)(S - Sc) * 4);
+    L.warps = L.smask + al16((size_t)S);
+    L.per_warp = al16((size_t)S * vsize) + (size_t)D * SU * vsize;
+    L.total = L.warps + (size_t)nw * L.per_warp;
+    return L;
+}
+
+__device__ __forceinline__ void ilu_cp16(void *sdst, const void *gsrc)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void ilu_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void ilu_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// first lower slot >= s of row (i,j,k) whose column is in the grid and in the pattern
+__device__ __forceinline__ int ilu_next(const StencilGeo &G, const unsigned char *smask, int s, int i, int j,
+                                        int k)
+{
+    for (; s < G.Sc; ++s) {
+        if (!smask[s]) continue;
+        int dx, dy, dz;
+        slot_offsets(G, s, dx, dy, dz);
+        const int ci = i + dx, cj = j + dy, ck = k + dz;
+        if (ci >= 0 && ci < G.n1 && cj >= 0 && cj < G.n1 && ck >= 0 && ck < G.n1) return s;
+    }
+    return G.Sc;
+}
+
+struct IluRow {
+    int i, j, k;
+    long long r;
+};
+
+// Fetch the U row used by step s into ring buffer q (all lanes issue 16-byte
+// copies).  When s opens a new line, first wait for the completion flags of
+// all rows of that line the elimination uses.  Returns false if a wait gave up.
 template <typename V>
-__global__ void __launch_bounds__(256) k_ilu0(StencilGeo G, V *Lv, V *Uv, const int *order,
-                                              unsigned *rowflag, unsigned *counter, int *err)
+__device__ __forceinline__ bool ilu_issue(const StencilGeo &G, const IluRow &R, const unsigned char *smask,
+                                          const unsigned *rowflag, int *err, const V *Uv, V *ring, int s, int q,
+                                          int &pseg)
 {
     const int lane = threadIdx.x & 31;
+    const int seg = s / G.W1;
+    if (seg != pseg) {
+        pseg = seg;
+        const int s0 = seg * G.W1, s1 = min(s0 + G.W1, G.Sc);
+        bool mine = true;
+        for (int t = s0 + lane; t < s1; t += 32) {
+            int dx, dy, dz;
+            slot_offsets(G, t, dx, dy, dz);
+            const int ci = R.i + dx, cj = R.j + dy, ck = R.k + dz;
+            if (!smask[t] || ci < 0 || ci >= G.n1 || cj < 0 || cj >= G.n1 || ck < 0 || ck >= G.n1) continue;
+            const long long kr = R.r + dx + (long long)G.n1 * (dy + (long long)G.n1 * dz);
+            mine = mine && wait_flag(rowflag + kr, 1u, err);
+        }
+        if (!__all_sync(0xffffffffu, mine)) return false;
+    }
+    int dx, dy, dz;
+    slot_offsets(G, s, dx, dy, dz);
+    const long long kr = R.r + dx + (long long)G.n1 * (dy + (long long)G.n1 * dz);
+    constexpr int CE = 16 / (int)sizeof(V);
+    const V *src = Uv + kr * G.SU;
+    V *dst = ring + (size_t)q * G.SU;
+    for (int c = lane; c < G.SU / CE; c += 32) ilu_cp16(dst + c * CE, src + c * CE);
+    return true;
+}
+
+template <typename V, int D>
+__global__ void __launch_bounds__(32 * ILU_MAX_WARPS) k_ilu0(StencilGeo G, V *Lv, V *Uv, const int *order,
+                                                            unsigned *rowflag, unsigned *counter, int *err)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int S = G.S, Sc = G.Sc, nU = S - Sc, SU = G.SU;
+    const IluSmem Lo = ilu_layout(S, Sc, SU, D, (int)sizeof(V), nw);
+    int *meta = (int *)(smem + Lo.meta);                 // offset (ex,ey,ez) of upper slot u, biased bytes
+    unsigned char *smask = smem + Lo.smask;             // structural flag per slot
+    V *a = (V *)(smem + Lo.warps + (size_t)wid * Lo.per_warp);
+    V *ring = (V *)((unsigned char *)a + al16((size_t)S * sizeof(V)));
+    for (int u = threadIdx.x; u < nU; u += blockDim.x) {
+        int ex, ey, ez;
+        slot_offsets(G, Sc + u, ex, ey, ez);
+        meta[u] = (ex + 128) | ((ey + 128) << 8) | ((ez + 128) << 16);
+    }
+    for (int t = threadIdx.x; t < S; t += blockDim.x) {
+        int dx, dy, dz;
+        slot_offsets(G, t, dx, dy, dz);
+        smask[t] = structural(G, dx, dy, dz) ? 1 : 0;
+    }
+    __syncthreads();
+
     for (;;) {
         long long idx = 0;
         if (lane == 0) idx = atomicAdd(counter, 1u);
         idx = __shfl_sync(0xffffffffu, idx, 0);
         if (idx >= G.n) return;
+        if (*(volatile int *)err != 0) return;
         const long long r = order[idx];
         const int i = (int)(r % G.n1);
         const int j = (G.d >= 2) ? (int)((r / G.n1) % G.n1) : 0;
         const int k = (G.d == 3) ? (int)(r / ((long long)G.n1 * G.n1)) : 0;
-        V *Lr = Lv + r * G.SL;
-        V *Ur = Uv + r * G.SU;
-        const double mii = (double)Ur[0];
-        int seg_dy = 1 << 20, seg_dz = 1 << 20;
-        bool ok = true;
-        for (int s = 0; s < G.Sc && ok; ++s) {
-            int dx, dy, dz;
-            slot_offsets(G, s, dx, dy, dz);
-            int ci = i + dx, cj = j + dy, ck = k + dz;
-            if (ci < 0 || ci >= G.n1 || cj < 0 || cj >= G.n1 || ck < 0 || ck >= G.n1) continue;
-            if (!structural(G, dx, dy, dz)) continue;
-            if (dy != seg_dy || dz != seg_dz) {
-                seg_dy = dy;
-                seg_dz = dz;
-                long long last;
-                if (dy == 0 && dz == 0)
-                    last = r - 1;
-                else
-                    last = (long long)min(i + G.w, G.n1 - 1) + G.n1 * ((long long)cj + (long long)G.n1 * ck);
-                ok = wait_flag(rowflag + last, 1u, err);
-                ok = __all_sync(0xffffffffu, ok);
-                if (!ok) break;
-            }
-            const long long kc = r + dx + (long long)G.n1 * (dy + (long long)G.n1 * dz);
-            const V *Uk = Uv + kc * G.SU;
-            __syncwarp();
-            V hrk = Lr[s] / __ldcg(Uk);
-            __syncwarp();
-            if (lane == 0) Lr[s] = hrk;
-            for (int u = 1 + lane; u <= G.Sc; u += 32) {
-                int ex, ey, ez;
-                slot_offsets(G, G.Sc + u, ex, ey, ez);
-                int tx = dx + ex, ty = dy + ey, tz = dz + ez;
-                if (tx < -G.w || tx > G.w || ty < -G.w || ty > G.w || tz < -G.w || tz > G.w) continue;
-                int ti = i + tx, tj = j + ty, tk = k + tz;
-                if (ti < 0 || ti >= G.n1 || tj < 0 || tj >= G.n1 || tk < 0 || tk >= G.n1) continue;
-                if (!structural(G, tx, ty, tz)) continue;
-                V ukj = __ldcg(Uk + u);
-                int ts = slot_index(G, tx, ty, tz);
-                if (ts < G.Sc)
-                    Lr[ts] -= hrk * ukj;
-                else
-                    Ur[ts - G.Sc] -= hrk * ukj;
-            }
-            __syncwarp();
-        }
+        for (int t = lane; t < Sc; t += 32) a[t] = Lv[r * G.SL + t];
+        for (int u = lane; u < nU; u += 32) a[Sc + u] = Uv[r * SU + u];
         __syncwarp();
-        if (lane == 0 && ok) {
-            double uii = (double)Ur[0];
-            if (!(uii > 1e-14 * fabs(mii))) set_err(err, DERR_BREAKDOWN);
+        const V mii = a[Sc];
+
+        // producer cursor: next step whose U row is fetched, and the line whose flags were checked
+        int ps = ilu_next(G, smask, 0, i, j, k), pseg = -1;
+        bool ok = true;
+        const IluRow R{i, j, k, r};
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            if (ps < Sc && ok) {
+                ok = ilu_issue<V>(G, R, smask, rowflag, err, Uv, ring, ps, q, pseg) && ok;
+                ps = ilu_next(G, smask, ps + 1, i, j, k);
+            }
+            ilu_commit();
         }
+        int cs = ilu_next(G, smask, 0, i, j, k), q = 0;
+        while (cs < Sc && ok) {
+            ilu_wait<D - 1>();
+            __syncwarp();
+            const V *Uk = ring + (size_t)q * SU;
+            const V l = a[cs] * Uk[SU - 1];  // H(r,k) / U(k,k) by the stored reciprocal pivot
+            int dx, dy, dz;
+            slot_offsets(G, cs, dx, dy, dz);
+            for (int u = 1 + lane; u < nU; u += 32) {
+                const int m = meta[u];
+                const int tx = dx + (m & 255) - 128, ty = dy + ((m >> 8) & 255) - 128, tz = dz + ((m >> 16) & 255) - 128;
+                if (tx < -G.w || tx > G.w || ty < -G.w || ty > G.w || tz < -G.w || tz > G.w) continue;
+                if (!smask[cs + u]) continue;
+                a[cs + u] -= l * Uk[u];
+            }
+            __syncwarp();
+            if (lane == 0) a[cs] = l;
+            if (ps < Sc && ok) {
+                ok = ilu_issue<V>(G, R, smask, rowflag, err, Uv, ring, ps, q, pseg) && ok;
+                ps = ilu_next(G, smask, ps + 1, i, j, k);
+            }
+            ilu_commit();
+            q = (q + 1 == D) ? 0 : q + 1;
+            cs = ilu_next(G, smask, cs + 1, i, j, k);
+        }
+        ilu_wait<0>();
+        __syncwarp();
+        if (!ok) return;  // a wait gave up: the error word is set, other warps stop too
+        const V uii = a[Sc];
+        if (lane == 0 && !((double)uii > 1e-14 * fabs((double)mii))) set_err(err, DERR_BREAKDOWN);
+        for (int t = lane; t < Sc; t += 32) Lv[r * G.SL + t] = a[t];
+        for (int u = lane; u < nU; u += 32) Uv[r * SU + u] = a[Sc + u];
+        if (lane == 0) Uv[r * SU + SU - 1] = V(1) / uii;
         __threadfence();
         __syncwarp();
         if (lane == 0) st_release(rowflag + r, 1u);
     }
+}
+
+template <typename V, int D>
+static int launch_ilu0_d(lsg_ctx *c, const StencilGeo &G, int nsm, cudaStream_t s)
+{
+    const size_t budget = 200 * 1024;
+    const IluSmem one = ilu_layout(G.S, G.Sc, G.SU, D, (int)sizeof(V), 1);
+    if (one.total > budget) return LSG_ERR_ARG;  // stencil too wide for a shared-memory row
+    int nw = (int)std::min<size_t>(ILU_MAX_WARPS, 1 + (budget - one.total) / one.per_warp);
+    const size_t smem = ilu_layout(G.S, G.Sc, G.SU, D, (int)sizeof(V), nw).total;
+    LSG_CK(cudaFuncSetAttribute(k_ilu0<V, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    LSG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ilu0<V, D>, 32 * nw, smem));
+    if (per_sm < 1) return LSG_ERR_ARG;
+    long long ctas = std::min<long long>((long long)nsm * per_sm, (G.n + nw - 1) / nw);
+    ::lsg::count_launch();
+    k_ilu0<V, D><<<(unsigned)ctas, 32 * nw, smem, s>>>(G, (V *)c->Lv, (V *)c->Uv, c->order, c->rowflag,
+                                                        c->counters, c->err);
+    LSG_CK(cudaGetLastError());
+    return LSG_OK;
+}
+
+template <typename V>
+static int launch_ilu0(lsg_ctx *c, const StencilGeo &G, int nsm, cudaStream_t s)
+{
+    // ring depth: four U rows in flight for lines (1D/2D), two for the wide 3D rows
+    if (G.d <= 2) return launch_ilu0_d<V, 4>(c, G, nsm, s);
+    return launch_ilu0_d<V, 2>(c, G, nsm, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -281,11 +417,7 @@ static int assemble_and_factor(lsg_ctx *c, cudaStream_t s)
     int dev = 0, nsm = 0;
     LSG_CK(cudaGetDevice(&dev));
     LSG_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    long long warps = std::min<long long>(g.n, (long long)nsm * 32);
-    unsigned blocks = (unsigned)((warps + 7) / 8);
-    ::lsg::count_launch();
-    k_ilu0<V><<<blocks, 256, 0, s>>>(G, (V *)c->Lv, (V *)c->Uv, c->order, c->rowflag, c->counters, c->err);
-    LSG_CK(cudaGetLastError());
+    LSG_TRY(launch_ilu0<V>(c, G, nsm, s));
     LSG_CK(cudaEventRecord(e2, s));
     LSG_CK(cudaEventSynchronize(e2));
     LSG_CK(cudaEventElapsedTime(&c->t_assemble_ms, e0, e1));

@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
                     acc = warp_sum(acc);
                     if (lane == 0) {
                         AT val = srhs[b * n1 + i] - acc;
-                        if (DIR < 0) val = val / (AT)row[-1];
+                        if (DIR < 0) val = val * (AT)row[RL - 2];  // 1 / U(i,i), stored by the factorisation
                         sy[myrow + i] = val;
                     }
                 }

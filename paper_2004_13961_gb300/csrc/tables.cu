@@ -26,7 +26,7 @@ Geom make_geom(int d, int N, int T, int Q)
     for (int i = 0; i < d; ++i) g.S *= g.W1;
     g.Sc = (g.S - 1) / 2;
     g.SL = (g.Sc + 7) / 8 * 8;        // 32-byte aligned rows in FP32, 64 in FP64
-    g.SU = (g.Sc + 1 + 7) / 8 * 8;
+    g.SU = (g.Sc + 2 + 7) / 8 * 8;    // diagonal, Sc upper slots, and a pad slot holding 1 / U_ii
     g.ne = (g.n1 + 1) / 2;
     g.no = g.n1 / 2;
     g.KP = (g.ne + 63) / 64 * 64;

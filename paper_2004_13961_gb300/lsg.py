@@ -279,3 +279,51 @@ def batch_solve(ctxs, Fs, us, rtol=1e-12, kmax=10000, stream=None):
     infos = (LsgInfo * n)()
     st = L.lsg_batch_solve(n, H, Fp, Up, float(rtol), int(kmax), infos, _stream(stream))
     return st, [i.as_dict() for i in infos]
+
+
+class Server:
+    """Continuous batching of solve requests (lsg_server_*): requests are admitted as
+    worker slots and HBM budget free up, and run on their own streams."""
+
+    def __init__(self, hbm_budget, max_inflight=4):
+        L = load()
+        self._L = L
+        h = ctypes.c_void_p(0)
+        _check(L.lsg_server_create(ctypes.byref(h), int(hbm_budget), int(max_inflight)), "lsg_server_create")
+        self._h = h
+
+    def submit(self, rid, d, N, T, a, b, f, Q=None, precision=FP64, rtol=1e-10, kmax=10000):
+        """Queue one request; a, b, f are host float64 arrays of Q^d samples (copied)."""
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        req = LsgRequest(id=int(rid), d=d, N=N, T=T, Q=(N + 2 if Q is None else Q), precision=precision,
+                         rtol=float(rtol), kmax=int(kmax), a=a.ctypes.data, b=b.ctypes.data, f=f.ctypes.data)
+        return self._L.lsg_server_submit(self._h, ctypes.byref(req))
+
+    def poll(self, max_results=64):
+        """Finished results: dicts with id, info, latency_ms and the solution (numpy copy)."""
+        out = (LsgResult * max_results)()
+        cnt = ctypes.c_int(0)
+        _check(self._L.lsg_server_poll(self._h, out, max_results, ctypes.byref(cnt)), "lsg_server_poll")
+        res = []
+        for k in range(cnt.value):
+            r = out[k]
+            u = np.ctypeslib.as_array(r.u, shape=(r.n,)).copy() if r.n > 0 and r.u else None
+            res.append(dict(id=r.id, info=r.info.as_dict(), latency_ms=r.latency_ms, u=u))
+            self._L.lsg_server_release(self._h, ctypes.byref(out[k]))
+        return res
+
+    def drain(self):
+        _check(self._L.lsg_server_drain(self._h), "lsg_server_drain")
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            self._L.lsg_server_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -44,6 +44,8 @@ CASES = [
     (3, 10, 2, 2, True),
     (3, 9, 2, 1, True),      # odd Q
     (2, 3, 1, 2, True),      # smallest N (one unknown per direction: n1 = 2)
+    (2, 20, 0, 2, False),    # T = 0 and b == 0: even offsets only, rows of a line finish out of order
+    (2, 96, 8, 2, True),     # many wavefront levels and warps in flight
 ]
 
 
