@@ -37,7 +37,6 @@ namespace lsg {
 constexpr int SW_MAXB = 8;   // compute warps (lines) per CTA
 constexpr int SW_HELP = 3;   // helper warps: TMA producer, halo loader, publisher
 constexpr int SW_D = 6;      // factor ring depth (rows in flight per line)
-constexpr int SW_PUB = 4;    // positions between progress publications
 constexpr int SW_KS = 16;    // register-resident slots per lane (1D/2D path)
 
 struct SweepArgs {
@@ -157,6 +156,25 @@ __host__ __device__ inline SweepSmem sweep_layout(int n1, int w, int B, int RL, 
     return L;
 }
 
+// Bounded spin until a shared counter reaches `need`: tight polls first (the
+// producer is a warp of this CTA a few hundred cycles away), then sleeps.
+__device__ __forceinline__ bool wait_count(const volatile int *c, int need, const volatile int *abort_flag, int *err)
+{
+    if (*c >= need) return true;
+    const long long t0 = clock64();
+    for (int it = 0;; ++it) {
+        if (*c >= need) return true;
+        if (it >= 64) __nanosleep(32);
+        if ((it & 15) == 15) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > kSpinBudgetCycles) {
+                set_err(err, DERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
 template <typename V, typename AT, int DIR>
 __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid_constant__ SweepArgs A)
 {
@@ -174,10 +192,12 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
     uint64_t *mbar = (uint64_t *)(smem + Lo.mbar);
     unsigned *meta = (unsigned *)(smem + Lo.meta);
     __shared__ volatile int s_abort;
-    __shared__ unsigned s_tick;      // ticks finished by the compute warps
-    __shared__ unsigned s_halo;      // virtual positions of every halo line staged in shared memory
+    __shared__ volatile int s_prog[SW_MAXB];  // positions finished by each line of the band
+    __shared__ volatile int s_near;           // positions of the line before the band staged in shared memory
+    __shared__ volatile int s_far;            // ... of every older halo line (minimum)
+    __shared__ int s_fresh[2];                // slots of the two newest dependencies (own line, previous line)
     __shared__ long long sband;
-    __shared__ int s_issued[SW_MAXB];  // factor rows the producer issued per line (this band)
+    __shared__ int s_issued[SW_MAXB];         // factor rows the producer issued per line (this band)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int role = wid - B;  // < 0: compute warp; 0: TMA producer; 1: halo loader; 2: publisher
     const AT *rhs = (const AT *)A.rhs;
@@ -191,8 +211,13 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
         int dx, dy, dz;
         slot_offsets(G, s, dx, dy, dz);
         meta[t] = (unsigned)(dx + 128) | ((unsigned)(dy + 128) << 8) | ((unsigned)(dz + 128) << 16);
+        // in sweep order the newest dependencies of a row are the previous position of
+        // its own line and position +w of the previous line
+        if (dx == -DIR && dy == 0 && dz == 0) s_fresh[0] = t;
+        if (G.d >= 2 && dx == DIR * w && dy == -DIR && dz == 0) s_fresh[1] = t;
     }
     if (threadIdx.x == 0) {
+        if (G.d < 2) s_fresh[1] = -1;
         for (int i = 0; i < B * SW_D; ++i) mbar_init(&mbar[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -205,17 +230,16 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
         __syncthreads();
         if (threadIdx.x == 0) {
             sband = atomicAdd(A.counter, 1u);
-            s_tick = 0;
-            s_halo = 0;
+            for (int b = 0; b < SW_MAXB; ++b) s_prog[b] = 0, s_issued[b] = 0;
+            s_near = 0;
+            s_far = 0;
             s_abort = (*(volatile int *)A.err != 0) ? 1 : 0;
-            for (int b = 0; b < SW_MAXB; ++b) s_issued[b] = 0;
         }
         __syncthreads();
         const long long band = sband;
         if (band >= nb) return;
         const long long v0 = band * B;
         const int nbl = (int)min((long long)B, G.nlines - v0);
-        const int nt = n1 + (w + 1) * (nbl - 1);
         // row buffers: rows 0..w-1 hold the halo (virtual lines v0-w..v0-1), rows
         // w..w+B-1 the band; position q of a row sits at rowoff[row] + q, aligned
         // like the line in global memory so 16-byte copies land on 16-byte boundaries
@@ -234,25 +258,26 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
             const long long line = DIR > 0 ? v0 + wid : G.nlines - 1 - (v0 + wid);
             for (int q = lane; q < n1; q += 32) srhs[wid * n1 + q] = rhs[q + (long long)n1 * line];
         }
+        if (threadIdx.x == 0 && v0 == 0) s_near = n1, s_far = n1;  // the first band has no halo
         __syncthreads();
 
         if (role == 0) {
             // -------------------------------------------------------------- TMA producer
-            // row q of line b goes to ring slot q % D once row q - D (same slot) has
-            // been consumed, i.e. after tick q - D + (w+1) b
+            // row q of line b goes to ring slot q % D once row q - D (same slot) is no
+            // longer read, i.e. once the line has finished position q - D
             if (lane == 0 && !aborted) {
                 const unsigned rowbytes = (unsigned)(RL * sizeof(V));
                 int q[SW_MAXB];
                 for (int b = 0; b < SW_MAXB; ++b) q[b] = (b < nbl) ? 0 : n1;
                 const long long t0 = clock64();
-                for (;;) {
-                    const int tk = (int)*(volatile unsigned *)&s_tick;
-                    __threadfence_block();
+                for (int it = 0;; ++it) {
                     if (s_abort) break;
                     bool all = true, any = false;
                     for (int b = 0; b < nbl; ++b) {
+                        const int fin = s_prog[b];
+                        __threadfence_block();
                         const long long line = DIR > 0 ? v0 + b : G.nlines - 1 - (v0 + b);
-                        while (q[b] < n1 && q[b] - SW_D + 1 + (w + 1) * b <= tk) {
+                        while (q[b] < n1 && q[b] - SW_D + 1 <= fin) {
                             if (!any) fence_proxy_async();
                             any = true;
                             const int p = q[b];
@@ -267,7 +292,7 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
                     }
                     if (all) break;
                     if (!any) {
-                        __nanosleep(32);
+                        if (it > 64) __nanosleep(32);
                         if (clock64() - t0 > 4 * kSpinBudgetCycles) {
                             set_err(A.err, DERR_TIMEOUT);
                             break;
@@ -280,7 +305,8 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
             // -------------------------------------------------------------- halo loader
             // lane h-1 stages virtual line v0-h: copies every 16-byte chunk whose
             // positions of that line are finished (progress acquired from global
-            // memory), waits for the copies, then publishes the common ready count
+            // memory), waits for the copies, then publishes how far the nearest line
+            // and the older ones are staged
             const bool hl = lane < w && (v0 - 1 - lane) >= 0 && !aborted;
             const long long hv = v0 - 1 - lane;
             const long long hline = hl ? (DIR > 0 ? hv : G.nlines - 1 - hv) : 0;
@@ -290,8 +316,8 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
             AT *hrow = sy + (hl ? rowoff[w - 1 - lane] : 0);
             const long long lo = hline * n1, hi = lo + n1 - 1;
             const long long t0 = clock64();
-            bool live = !aborted;
-            while (live) {
+            bool live = v0 > 0 && !aborted;
+            for (int it = 0; live; ++it) {
                 if (hvis < n1) {
                     const unsigned P = ld_acquire(A.gprog + hline);
                     for (;;) {
@@ -314,13 +340,15 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
                 }
                 cp_async_commit();
                 cp_async_wait<0>();
-                const int ready = __reduce_min_sync(0xffffffffu, (unsigned)hvis);
+                const int near = __shfl_sync(0xffffffffu, hvis, 0);
+                const int far = (int)__reduce_min_sync(0xffffffffu, (unsigned)(lane == 0 ? n1 : hvis));
                 if (lane == 0) {
                     __threadfence_block();
-                    *(volatile unsigned *)&s_halo = (unsigned)ready;
+                    s_far = far;
+                    s_near = near;
                 }
-                if (ready >= n1) break;
-                __nanosleep(64);
+                if (near >= n1 && far >= n1) break;
+                if (it > 32) __nanosleep(32);
                 // warp-uniform exits (the loop uses full-warp collectives)
                 if (__any_sync(0xffffffffu, s_abort != 0)) break;
                 if (__any_sync(0xffffffffu, clock64() - t0 > 4 * kSpinBudgetCycles)) {
@@ -330,17 +358,19 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
             }
         } else if (role == 2) {
             // -------------------------------------------------------------- publisher
+            // copies each line's finished positions to global memory and releases its
+            // progress word; every pass publishes whatever the lines finished meanwhile
             const bool mine = lane < nbl;
             const long long line = DIR > 0 ? v0 + lane : G.nlines - 1 - (v0 + lane);
-            int pub = 0, rel = 0;
+            int pub = 0;
             bool finished = !mine;
             const long long t0 = clock64();
-            while (!__all_sync(0xffffffffu, finished)) {
-                const int tk = (int)*(volatile unsigned *)&s_tick;
+            for (int it = 0; !__all_sync(0xffffffffu, finished); ++it) {
                 const bool ab = s_abort != 0;
+                const int fin = (mine && !finished) ? (ab ? n1 : s_prog[lane]) : 0;
                 __threadfence_block();
-                if (mine && !finished) {
-                    const int fin = ab ? n1 : max(0, min(tk - (w + 1) * lane, n1));
+                bool moved = false;
+                if (mine && !finished && fin > pub) {
                     if (!ab) {
                         const int row = rowoff[w + lane];
                         for (; pub < fin; ++pub) {
@@ -348,15 +378,15 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
                             out[i + (long long)n1 * line] = sy[row + i];
                         }
                     }
-                    if (fin >= rel + SW_PUB || fin == n1) {
-                        __threadfence();
-                        st_release(A.gprog + line, (unsigned)fin);
-                        rel = fin;
-                        if (fin == n1) finished = true;
-                    }
+                    pub = fin;
+                    moved = true;
                 }
-                if (!__all_sync(0xffffffffu, finished)) {
-                    __nanosleep(64);
+                if (__any_sync(0xffffffffu, moved)) {
+                    __threadfence();
+                    if (moved) st_release(A.gprog + line, (unsigned)pub);
+                    if (moved && pub == n1) finished = true;
+                } else {
+                    if (it > 64) __nanosleep(32);
                     if (clock64() - t0 > 4 * kSpinBudgetCycles) {  // the compute warps' waits are bounded
                         set_err(A.err, DERR_TIMEOUT);
                         finished = true;
@@ -365,6 +395,9 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
             }
         } else {
             // -------------------------------------------------------------- compute warp
+            // Position q of the line: y_q = (r_q - S_q - l_own y_{q-1} - l_prev y'_{q+w}) [/ U_qq],
+            // where S_q (every other term of the row) is computed one position ahead,
+            // while the line waits for y_{q-1} and the previous line's y'_{q+w}.
             const int b = wid;
             const bool live = b < nbl;
             const long long v = v0 + b;
@@ -377,8 +410,11 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
             if (live && G.d == 3 && kv >= 1) vplane = (long long)min(jv + w, n1 - 1) + (long long)n1 * (kv - 1);
             const long long plane_real = vplane < 0 ? -1 : (DIR > 0 ? vplane : G.nlines - 1 - vplane);
             unsigned seen_plane = 0;
+            const int f_own = s_fresh[0], f_prev = s_fresh[1];
+            const int nk = (nslot + 31) / 32;  // slots per lane
             // register-resident stencil: offset of each of this lane's slots in the row buffers
             int off[SW_KS];
+            unsigned freshmask = 0;
 #pragma unroll
             for (int kk = 0; kk < SW_KS; ++kk) {
                 const int t = lane + 32 * kk;
@@ -388,69 +424,105 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
                     const int dx = (int)(m & 255u) - 128, dy = (int)((m >> 8) & 255u) - 128;
                     off[kk] = rowoff[b + w + DIR * dy] + dx;
                 }
+                if (t == f_own || t == f_prev) freshmask |= 1u << kk;
             }
             const V *myring = ring + (size_t)b * SW_D * RL;
             uint64_t *mybar = mbar + b * SW_D;
             const int myrow = rowoff[b + w];
-            bool ok = !aborted;
-            int tick = 0;
-            for (; tick < nt && ok; ++tick) {
-                const int p = tick - (w + 1) * b;
-                const bool act = live && p >= 0 && p < n1;
-                if (act) {
-                    // halo lines (only bands after the first have any) up to position p + w
-                    if (v0 > 0 && b < w) ok = wait_smem_at_least(&s_halo, (unsigned)min(tick + w + 1, n1), &s_abort, A.err);
-                    const int slot = p % SW_D;
-                    if (ok && !mbar_wait(&mybar[slot], (phase >> slot) & 1u, A.err)) ok = false;
-                    phase ^= 1u << slot;
-                    if (vplane >= 0 && ok)
-                        ok = wait_flag_cached(A.gprog + plane_real, (unsigned)min(p + w + 1, n1), A.err, &seen_plane);
-                    ok = __all_sync(0xffffffffu, ok);
-                    __threadfence_block();
-                }
-                if (act && ok) {
-                    const int i = DIR > 0 ? p : n1 - 1 - p;
-                    const V *row = myring + (size_t)(p % SW_D) * RL + (DIR > 0 ? 0 : 1);
-                    AT acc = 0;
-                    if (regpath) {
+            // the previous line's buffer row and the stencil offset of its newest dependency
+            const int prevoff = rowoff[b + w - 1] + DIR * w;
+            const volatile int *prevc = (b == 0) ? &s_near : &s_prog[b - 1];
+            bool ok = live && !aborted;
+            int waited = 0;  // factor rows whose ring slot this warp has waited for
+
+            // wait until position q (sweep order) may be finished and S_{q+1} computed:
+            // previous line up to q+w, older lines up to q+w+1, other planes likewise
+            auto wait_deps = [&](int q) -> bool {
+                bool good = wait_count(prevc, min(q + w + 1, n1), &s_abort, A.err);
+                if (good && b == 0) good = wait_count(&s_far, min(q + w + 2, n1), &s_abort, A.err);
+                if (good && vplane >= 0)
+                    good = wait_flag_cached(A.gprog + plane_real, (unsigned)min(q + w + 2, n1), A.err, &seen_plane);
+                good = __all_sync(0xffffffffu, good);
+                __threadfence_block();
+                return good;
+            };
+            // S_q: the row's dot product without its two newest terms (all lanes get it)
+            auto stale = [&](int q) -> AT {
+                const int i = DIR > 0 ? q : n1 - 1 - q;
+                const V *row = myring + (size_t)(q % SW_D) * RL + (DIR > 0 ? 0 : 1);
+                AT acc0 = 0, acc1 = 0;
+                if (regpath) {
+                    // a warp-uniform trip count: an FP64 instruction costs its full issue
+                    // time even when every lane is predicated off
 #pragma unroll
-                        for (int kk = 0; kk < SW_KS; ++kk) {
-                            const int t = lane + 32 * kk;
-                            if (t < nslot) acc += (AT)row[t] * sy[off[kk] + i];
-                        }
-                    } else {
-                        for (int t = lane; t < nslot; t += 32) {
-                            const unsigned m = meta[t];
-                            const int dx = (int)(m & 255u) - 128, dy = (int)((m >> 8) & 255u) - 128,
-                                      dz = (int)((m >> 16) & 255u) - 128;
-                            const int ci = i + dx, cj = j + dy, ck = k + dz;
-                            if (ci < 0 || ci >= n1 || cj < 0 || cj >= n1 || ck < 0 || ck >= n1) continue;
-                            AT yv;
-                            if (dz == 0)
-                                yv = sy[rowoff[b + w + DIR * dy] + ci];
-                            else
-                                yv = __ldcg(out + ci + (long long)n1 * (cj + (long long)n1 * ck));
-                            acc += (AT)row[t] * yv;
-                        }
+                    for (int kk = 0; kk < SW_KS; kk += 2) {
+                        if (kk >= nk) break;
+                        const int t0 = lane + 32 * kk, t1 = t0 + 32;
+                        if (t0 < nslot && !(freshmask >> kk & 1u)) acc0 += (AT)row[t0] * sy[off[kk] + i];
+                        if (kk + 1 < nk && t1 < nslot && !(freshmask >> (kk + 1) & 1u))
+                            acc1 += (AT)row[t1] * sy[off[kk + 1] + i];
                     }
-                    acc = warp_sum(acc);
-                    if (lane == 0) {
-                        AT val = srhs[b * n1 + i] - acc;
-                        if (DIR < 0) val = val * (AT)row[RL - 2];  // 1 / U(i,i), stored by the factorisation
-                        sy[myrow + i] = val;
+                } else {
+                    for (int t = lane; t < nslot; t += 32) {
+                        if (t == f_own || t == f_prev) continue;
+                        const unsigned m = meta[t];
+                        const int dx = (int)(m & 255u) - 128, dy = (int)((m >> 8) & 255u) - 128,
+                                  dz = (int)((m >> 16) & 255u) - 128;
+                        const int ci = i + dx, cj = j + dy, ck = k + dz;
+                        if (ci < 0 || ci >= n1 || cj < 0 || cj >= n1 || ck < 0 || ck >= n1) continue;
+                        AT yv;
+                        if (dz == 0)
+                            yv = sy[rowoff[b + w + DIR * dy] + ci];
+                        else
+                            yv = __ldcg(out + ci + (long long)n1 * (cj + (long long)n1 * ck));
+                        acc0 += (AT)row[t] * yv;
                     }
                 }
-                if (!__all_sync(0xffffffffu, ok)) ok = false;
-                if (!ok && lane == 0) s_abort = 1;
-                named_barrier(1, 32 * B);
-                if (s_abort) ok = false;
-                if (b == 0 && lane == 0) {
+                return warp_sum(acc0 + acc1);
+            };
+            auto wait_row = [&](int q) -> bool {
+                const int slot = q % SW_D;
+                bool good = mbar_wait(&mybar[slot], (phase >> slot) & 1u, A.err);
+                phase ^= 1u << slot;
+                ++waited;
+                return __all_sync(0xffffffffu, good);
+            };
+
+            AT T = 0, yprev = 0;  // T = r_q - S_q of the next position; yprev = y_{q-1}
+            if (ok) ok = wait_deps(-1) && wait_row(0);
+            if (ok) {
+                const AT S = stale(0);
+                T = srhs[b * n1 + (DIR > 0 ? 0 : n1 - 1)] - S;
+            }
+            int q = 0;
+            for (; q < n1 && ok; ++q) {
+                const int i = DIR > 0 ? q : n1 - 1 - q;
+                ok = wait_deps(q);
+                if (!ok) break;
+                if (lane == 0) {
+                    const V *row = myring + (size_t)(q % SW_D) * RL + (DIR > 0 ? 0 : 1);
+                    AT val = T;
+                    if (f_prev >= 0) val -= (AT)row[f_prev] * sy[prevoff + i];
+                    val -= (AT)row[f_own] * yprev;
+                    if (DIR < 0) val = val * (AT)row[RL - 2];  // 1 / U(i,i), stored by the factorisation
+                    sy[myrow + i] = val;
+                    yprev = val;
                     __threadfence_block();
-                    *(volatile unsigned *)&s_tick = ok ? (unsigned)(tick + 1) : (unsigned)(nt + (w + 1) * B);
+                    s_prog[b] = q + 1;
+                }
+                __syncwarp();
+                if (q + 1 < n1) {
+                    if (!wait_row(q + 1)) {
+                        ok = false;
+                        break;
+                    }
+                    const AT S = stale(q + 1);
+                    T = srhs[b * n1 + (DIR > 0 ? q + 1 : n1 - 2 - q)] - S;
                 }
             }
-            consumed_rows = live ? max(0, min(tick - (w + 1) * b, n1)) : 0;
-            last_ok = ok;
+            if (live && !ok && lane == 0) s_abort = 1;
+            consumed_rows = waited;
+            last_ok = ok || !live;
         }
         // after an abort, wait (bounded) for factor rows the producer issued but this
         // warp did not consume, so no bulk copy lands in shared memory after the band
@@ -487,10 +559,12 @@ static int sweeps(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done, cud
     A.G = sgeo(g);
     A.done = done;
     A.err = c->err;
-    // lines per CTA: the largest that fits the shared-memory budget
+    // lines per CTA: one per SM sub-partition when the dot products run in FP64
+    // (an FP64 warp instruction occupies its sub-partition's FP64 unit for ~64
+    // clocks), two per sub-partition in FP32; fewer if shared memory runs out
     const size_t budget = 210 * 1024;
     const int RLmax = std::max(g.SL, g.SU);
-    int B = SW_MAXB;
+    int B = sizeof(AT) == 8 ? 4 : SW_MAXB;
     while (B > 1 && sweep_layout(g.n1, g.w, B, RLmax, (int)sizeof(V), g.Sc, (int)sizeof(AT)).total > budget) B /= 2;
     if (sweep_layout(g.n1, g.w, B, RLmax, (int)sizeof(V), g.Sc, (int)sizeof(AT)).total > budget) return LSG_ERR_ARG;
     if (g.w > 31) return LSG_ERR_ARG;  // one halo lane per previous line
