@@ -175,6 +175,14 @@ int lsg_load_vector(lsg_ctx *ctx, const double *f, double *F, lsg_stream_t strea
  * transforms).  x, y: n doubles; y must not alias x. */
 int lsg_apply_A(lsg_ctx *ctx, const double *x, double *y, lsg_stream_t stream);
 
+/* y = K x with the mixed form's low-precision transforms (Sec. 4.3, as
+ * lsg_apply_A): each contraction is a tensor-core GEMM with TF32
+ * (LSG_MIXED_TF32) or BF16 (LSG_MIXED_BF16) operands and FP32 accumulation;
+ * the pointwise products use FP32 copies of the weighted coefficients.
+ * x, y: n floats on the device; y must not alias x.  LSG_ERR_ARG for FP64
+ * contexts. */
+int lsg_apply_A_lowp(lsg_ctx *ctx, const float *x, float *y, lsg_stream_t stream);
+
 /* z = U^{-1} L^{-1} r: the one-step ILU(0) preconditioner solve (Sec. 4.2,
  * Algorithms 3 and 4).  r, z: n doubles; z must not alias r.  Mixed-precision
  * contexts sweep FP32 factors with FP32 accumulation. */

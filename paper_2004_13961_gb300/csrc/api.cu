@@ -62,7 +62,7 @@ int read_dev_error(lsg_ctx *c, cudaStream_t s)
 }
 
 struct Sizes {
-    size_t tab, tab32, grid, series, band, Lv, Uv, Mkeep, ws, vec, lines;
+    size_t tab, grid, series, band, Lv, Uv, Mkeep, ws, vec, lines;
 };
 
 static Sizes sizes_for(const Geom &g, int precision, unsigned flags)
@@ -72,7 +72,6 @@ static Sizes sizes_for(const Geom &g, int precision, unsigned flags)
     for (int i = 0; i < g.d; ++i) ns *= T1;
     size_t vsz = precision == LSG_FP64 ? 8 : 4;
     z.tab = 4 * (size_t)g.QhP * g.KP * 8;
-    z.tab32 = precision == LSG_FP64 ? 0 : 4 * (size_t)g.QhP * g.KP * 4;
     z.grid = (size_t)g.nq * 8;
     z.series = ns * 8;
     z.band = T1 * g.n1 * g.W1 * 8;
@@ -88,10 +87,11 @@ static Sizes sizes_for(const Geom &g, int precision, unsigned flags)
 static size_t footprint(const Geom &g, int precision, unsigned flags)
 {
     Sizes z = sizes_for(g, precision, flags);
-    size_t b = 2 * (size_t)g.Q * 8 + z.tab + z.tab32 + 3 * z.grid + 2 * z.series + 2 * z.band + z.Lv + z.Uv +
+    size_t b = 2 * (size_t)g.Q * 8 + z.tab + 3 * z.grid + 2 * z.series + 2 * z.band + z.Lv + z.Uv +
                z.Mkeep + z.ws + 7 * z.vec + (size_t)g.n * 4 * 2 + 2 * z.lines + 64 + kRedBlocks * 16 +
                sizeof(PcgState);
     if (precision != LSG_FP64) b += 6 * (size_t)g.n * 4 + 2 * (size_t)g.nq * 4 + 2 * z.vec + z.ws / 2;
+    b += tc_table_bytes(g, precision);
     // transient setup buffers: sample staging (2 grids) and the precontracted arrays
     size_t T1 = g.T + 1;
     size_t nK = g.d == 3 ? T1 * T1 : T1;
@@ -145,10 +145,10 @@ static int check_sizes(int d, int N, int T, int Q)
 static void free_ctx(lsg_ctx *c)
 {
     if (!c) return;
-    void *ptrs[] = {c->gx, c->gw, c->tab, c->tab32, c->Wa, c->Wb, c->Wg, c->ahat, c->bhat, c->bandS, c->bandM,
+    void *ptrs[] = {c->gx, c->gw, c->tab, c->Wa, c->Wb, c->Wg, c->ahat, c->bhat, c->bandS, c->bandM,
                     c->Lv, c->Uv, c->Mkeep, c->order, c->rowflag, c->prog, c->counters, c->err, c->ws, c->ws32,
                     c->r, c->z, c->p, c->wv, c->xs, c->fs, c->ys, c->red, c->st, c->r32, c->z32, c->p32, c->w32,
-                    c->e32, c->e64, c->u64, c->y32, c->Wa32, c->Wb32};
+                    c->e32, c->e64, c->u64, c->y32, c->Wa32, c->Wb32, c->tct};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->st_host) cudaFreeHost(c->st_host);
@@ -268,7 +268,6 @@ int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, con
     ALLOC(c->gx, sizeof(double) * Q);
     ALLOC(c->gw, sizeof(double) * Q);
     ALLOC(c->tab, z.tab);
-    if (z.tab32) ALLOC(c->tab32, z.tab32);
     ALLOC(c->Wa, z.grid);
     ALLOC(c->Wb, z.grid);
     ALLOC(c->Wg, z.grid);
@@ -306,6 +305,7 @@ int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, con
         ALLOC(c->e64, z.vec);
         ALLOC(c->u64, z.vec);
         ALLOC(c->ws32, z.ws / 2);
+        ALLOC(c->tct, tc_table_bytes(g, precision));
     }
     double *sa = nullptr, *sb = nullptr;
     bool ha = !is_device_ptr(a), hb = !is_device_ptr(b);
@@ -342,6 +342,8 @@ int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, con
     }
     if (cudaMemsetAsync(c->err, 0, sizeof(int) * 4, s) != cudaSuccess) return fail(LSG_ERR_CUDA);
     st = build_tables(c, da, db, s);
+    if (st != LSG_OK) return fail(st);
+    st = build_tc_tables(c, s);
     if (st != LSG_OK) return fail(st);
     int derr = read_dev_error(c, s);
     if (derr != LSG_OK) return fail(derr);
@@ -384,6 +386,14 @@ int lsg_load_vector(lsg_ctx *c, const double *f, double *F, lsg_stream_t stream)
         LSG_CK(cudaStreamSynchronize(s));
     }
     return LSG_OK;
+}
+
+int lsg_apply_A_lowp(lsg_ctx *c, const float *x, float *y, lsg_stream_t stream)
+{
+    if (!c || !x || !y || x == y || c->precision == LSG_FP64) return LSG_ERR_ARG;
+    if (!is_device_ptr(x) || !is_device_ptr(y)) return LSG_ERR_ARG;
+    LSG_TRY(apply_K_tc(c, x, y, nullptr, (cudaStream_t)stream));
+    return read_dev_error(c, (cudaStream_t)stream);
 }
 
 int lsg_apply_A(lsg_ctx *c, const double *x, double *y, lsg_stream_t stream)

@@ -78,9 +78,10 @@ struct lsg_ctx {
     // Gauss rule and folded transform tables (FP64)
     double *gx, *gw;           // Q nodes / weights
     double *tab;               // 4 blocks of QhP*KP: phiE, phiO, dphiE, dphiO
-    float *tab32;              // FP32 copies (mixed)
     double *Wa, *Wb, *Wg;      // w(x)w(y)w(z) * a, * b, and the weights alone (Q^d)
     float *Wa32, *Wb32;        // FP32 copies (mixed)
+    void *tct;                 // mixed: unfolded TF32/BF16 tables for the tensor-core contractions
+    int tcMpF, tcKpF, tcMpB, tcKpB;  // their padded shapes (forward [MpF][KpF], backward [MpB][KpB])
     double *ahat, *bhat;       // (T+1)^d
     double *bandS, *bandM;     // (T+1) x n1 x W1
 
@@ -123,7 +124,9 @@ bool is_device_ptr(const void *p);
 int build_tables(lsg_ctx *c, const double *a_dev, const double *b_dev, cudaStream_t s);
 int build_preconditioner(lsg_ctx *c, cudaStream_t s);
 int apply_K(lsg_ctx *c, const double *x, double *y, const int *done, cudaStream_t s);
-int apply_K32(lsg_ctx *c, const float *x, float *y, const int *done, cudaStream_t s);
+int apply_K_tc(lsg_ctx *c, const float *x, float *y, const int *done, cudaStream_t s);
+int build_tc_tables(lsg_ctx *c, cudaStream_t s);
+size_t tc_table_bytes(const Geom &g, int precision);
 int load_vector(lsg_ctx *c, const double *f, double *F, cudaStream_t s);
 int eval_grid(lsg_ctx *c, const double *u, double *vals, cudaStream_t s);
 int apply_Minv(lsg_ctx *c, const double *r, double *z, const int *done, cudaStream_t s);

@@ -109,7 +109,7 @@ __global__ void k_gauss(int Q, double *x, double *w)
 //   dE[q][m]   = phi'_{2m}(x_q),  dO[q][m]   = phi'_{2m+1}(x_q),
 // with phi_k = L_k - L_{k+2} and phi'_k = -(2k+3) L_{k+1} (Sec. 3 and the
 // derivative recurrence of Sec. 2.1).  Padding rows/columns are zero.
-__global__ void k_tables(int Q, int n1, int QhP, int KP, const double *x, double *tab, float *tab32)
+__global__ void k_tables(int Q, int n1, int QhP, int KP, const double *x, double *tab)
 {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= QhP) return;
@@ -120,7 +120,6 @@ __global__ void k_tables(int Q, int n1, int QhP, int KP, const double *x, double
     if (q >= Qh) {
         for (int m = 0; m < KP; ++m) {
             pE[row + m] = pO[row + m] = dE[row + m] = dO[row + m] = 0.0;
-            if (tab32) tab32[row + m] = tab32[blk + row + m] = tab32[2 * blk + row + m] = tab32[3 * blk + row + m] = 0.f;
         }
         return;
     }
@@ -140,17 +139,9 @@ __global__ void k_tables(int Q, int n1, int QhP, int KP, const double *x, double
         if (k & 1) {
             pO[row + m] = phi;
             dO[row + m] = dphi;
-            if (tab32) {
-                tab32[blk + row + m] = (float)phi;
-                tab32[3 * blk + row + m] = (float)dphi;
-            }
         } else {
             pE[row + m] = phi;
             dE[row + m] = dphi;
-            if (tab32) {
-                tab32[row + m] = (float)phi;
-                tab32[2 * blk + row + m] = (float)dphi;
-            }
         }
         // advance: degree k+3 from k+2 (c) and k+1 (b)
         double nk = k + 2.0;
@@ -311,7 +302,7 @@ int build_tables(lsg_ctx *c, const double *a_dev, const double *b_dev, cudaStrea
     k_gauss<<<blocks_for(g.Qh, 128), 128, 0, s>>>(g.Q, c->gx, c->gw);
     LSG_CK(cudaGetLastError());
     ::lsg::count_launch();
-    k_tables<<<blocks_for(g.QhP, 64), 64, 0, s>>>(g.Q, g.n1, g.QhP, g.KP, c->gx, c->tab, c->tab32);
+    k_tables<<<blocks_for(g.QhP, 64), 64, 0, s>>>(g.Q, g.n1, g.QhP, g.KP, c->gx, c->tab);
     LSG_CK(cudaGetLastError());
     ::lsg::count_launch();
     k_weighted<<<blocks_for(g.nq, 256), 256, 0, s>>>(g.d, g.Q, g.nq, c->gw, a_dev, b_dev, c->Wa, c->Wb,

@@ -242,10 +242,6 @@ static void job_init(XfJob<double> &j, const lsg_ctx *c, long long B, const int 
 {
     job_init_t<double>(j, c, c->tab, B, done);
 }
-static void job_init(XfJob<float> &j, const lsg_ctx *c, long long B, const int *done)
-{
-    job_init_t<float>(j, c, c->tab32, B, done);
-}
 template <typename T>
 struct ident {
     using type = T;
@@ -381,10 +377,6 @@ int apply_K(lsg_ctx *c, const double *x, double *y, const int *done, cudaStream_
     return apply_K_t<double>(c, x, y, done, c->ws, c->Wa, c->Wb, s);
 }
 
-int apply_K32(lsg_ctx *c, const float *x, float *y, const int *done, cudaStream_t s)
-{
-    return apply_K_t<float>(c, x, y, done, c->ws32, c->Wa32, c->Wb32, s);
-}
 
 __global__ void k_mul(long long n, const double *a, const double *b, double *out)
 {

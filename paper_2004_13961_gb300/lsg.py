@@ -37,7 +37,8 @@ OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_ILU_BREAKDOWN, ERR_NOT_CONVERGED, ERR_TIME
 # every symbol the header declares (checked by the ABI test)
 SYMBOLS = [
     "lsg_version", "lsg_status_string", "lsg_last_error", "lsg_kernel_launches", "lsg_gauss", "lsg_gauss_noalloc", "lsg_footprint_bytes",
-    "lsg_setup", "lsg_setup_ex", "lsg_load_vector", "lsg_apply_A", "lsg_apply_Minv", "lsg_pcg_solve",
+    "lsg_setup", "lsg_setup_ex", "lsg_load_vector", "lsg_apply_A", "lsg_apply_A_lowp", "lsg_apply_Minv",
+    "lsg_pcg_solve",
     "lsg_eval", "lsg_export_count", "lsg_export", "lsg_query", "lsg_destroy", "lsg_batch_solve",
     "lsg_server_create", "lsg_server_submit", "lsg_server_poll", "lsg_server_drain",
     "lsg_server_release", "lsg_server_destroy",
@@ -94,7 +95,7 @@ def load(build_if_needed: bool = True):
     L.lsg_footprint_bytes.restype = ctypes.c_size_t
     L.lsg_setup.argtypes = [ctypes.POINTER(vp), ci, ci, ci, ci, vp, vp, ci, vp]
     L.lsg_setup_ex.argtypes = [ctypes.POINTER(vp), ci, ci, ci, ci, vp, vp, ci, cu, vp]
-    for name in ("lsg_load_vector", "lsg_apply_A", "lsg_apply_Minv", "lsg_eval"):
+    for name in ("lsg_load_vector", "lsg_apply_A", "lsg_apply_A_lowp", "lsg_apply_Minv", "lsg_eval"):
         getattr(L, name).argtypes = [vp, vp, vp, vp]
     L.lsg_pcg_solve.argtypes = [vp, vp, vp, cd, ci, ctypes.POINTER(LsgInfo), vp]
     L.lsg_export_count.argtypes = [vp, ci]
@@ -228,6 +229,16 @@ class Context:
     def apply_A(self, x, y=None, stream=None):
         y = _like(x, self.n) if y is None else y
         _check(self._L.lsg_apply_A(self._h, _ptr(x), _ptr(y), _stream(stream)), "lsg_apply_A")
+        return y
+
+    def apply_A_lowp(self, x, y=None, stream=None):
+        """y = K x with the tensor-core transforms of a mixed context (float32 CUDA tensors)."""
+        if y is None:
+            y = torch.empty(self.n, dtype=torch.float32, device=x.device)
+        if x.dtype != torch.float32 or y.dtype != torch.float32 or not (x.is_contiguous() and y.is_contiguous()):
+            raise ValueError("expected contiguous float32 tensors")
+        _check(self._L.lsg_apply_A_lowp(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                        _stream(stream)), "lsg_apply_A_lowp")
         return y
 
     def apply_Minv(self, r, z=None, stream=None):
