@@ -155,27 +155,29 @@ __global__ void k_level_scatter(StencilGeo G, int *cursor, int *order)
 //
 // One warp per row, rows claimed in wavefront order (a warp only waits for
 // rows claimed earlier by running warps).  The row lives in shared memory for
-// the whole elimination; the U rows it needs are streamed into a per-warp ring
-// of D shared-memory buffers with 16-byte cp.async copies issued D steps
-// ahead, so a step is: one multiply by the stored reciprocal pivot and one
-// masked vector update, all in shared memory.  In stencil slot numbering the
-// target of U(k, slot Sc+u) is simply slot s+u of row r (s: the step's lower
-// slot), valid when the target offset stays in the box and in the pattern;
-// columns outside the grid hold exact zeros in both rows, so they need no
-// test.  Before the first U row of a line is fetched, the warp checks the
-// completion flags of every row it will use from that line (one per lane).
-// A finished row stores 1 / U(r,r) in the pad slot SU-1 of its U row.
+// the whole elimination.  In stencil slot numbering the target of U(k, Sc+u)
+// is slot s+u of row r (s: the step's lower slot), valid when the target
+// offset stays in the box and in the pattern; columns outside the grid hold
+// exact zeros in both rows, so they need no test.
+//
+// Each step waits only for its own row k (not for the whole line k belongs
+// to), so a row follows the rows it depends on closely: once the newest of
+// them finishes, only the last step or two remain.  The U rows of the next
+// D-1 steps are prefetched into a ring of shared-memory buffers with 16-byte
+// cp.async copies when their rows are already finished (checked without
+// blocking); a step whose row was not ready at prefetch time waits for it and
+// copies it then.  A finished row stores 1 / U(r,r) in the pad slot SU-1.
 constexpr int ILU_MAX_WARPS = 8;
 
 struct IluSmem {
-    size_t meta, smask, warps, per_warp, total;
+    size_t off, smask, warps, per_warp, total;
 };
 __host__ __device__ inline size_t al16(size_t b) { return (b + 15) / 16 * 16; }
-__host__ __device__ inline IluSmem ilu_layout(int S, int Sc, int SU, int D, int vsize, int nw)
+__host__ __device__ inline IluSmem ilu_layout(int S, int SU, int D, int vsize, int nw)
 {
     IluSmem L;
-    L.meta = 0;
-    L.smask = al16((size_t)(S - Sc) * 4);
+    L.off = 0;
+    L.smask = al16((size_t)S * 4);
     L.warps = L.smask + al16((size_t)S);
     L.per_warp = al16((size_t)S * vsize) + (size_t)D * SU * vsize;
     L.total = L.warps + (size_t)nw * L.per_warp;
@@ -192,79 +194,60 @@ __device__ __forceinline__ void ilu_commit() { asm volatile("cp.async.commit_gro
 template <int N>
 __device__ __forceinline__ void ilu_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// unpack a slot offset stored as three biased bytes
+__device__ __forceinline__ void ilu_off(int m, int &dx, int &dy, int &dz)
+{
+    dx = (m & 255) - 128;
+    dy = ((m >> 8) & 255) - 128;
+    dz = ((m >> 16) & 255) - 128;
+}
+
 // first lower slot >= s of row (i,j,k) whose column is in the grid and in the pattern
-__device__ __forceinline__ int ilu_next(const StencilGeo &G, const unsigned char *smask, int s, int i, int j,
-                                        int k)
+__device__ __forceinline__ int ilu_next(const StencilGeo &G, const int *off, const unsigned char *smask, int s,
+                                        int i, int j, int k)
 {
     for (; s < G.Sc; ++s) {
         if (!smask[s]) continue;
         int dx, dy, dz;
-        slot_offsets(G, s, dx, dy, dz);
+        ilu_off(off[s], dx, dy, dz);
         const int ci = i + dx, cj = j + dy, ck = k + dz;
         if (ci >= 0 && ci < G.n1 && cj >= 0 && cj < G.n1 && ck >= 0 && ck < G.n1) return s;
     }
     return G.Sc;
 }
 
-struct IluRow {
-    int i, j, k;
-    long long r;
-};
-
-// Fetch the U row used by step s into ring buffer q (all lanes issue 16-byte
-// copies).  When s opens a new line, first wait for the completion flags of
-// all rows of that line the elimination uses.  Returns false if a wait gave up.
-template <typename V>
-__device__ __forceinline__ bool ilu_issue(const StencilGeo &G, const IluRow &R, const unsigned char *smask,
-                                          const unsigned *rowflag, int *err, const V *Uv, V *ring, int s, int q,
-                                          int &pseg)
+__device__ __forceinline__ long long ilu_row_of(const StencilGeo &G, long long r, int m)
 {
-    const int lane = threadIdx.x & 31;
-    const int seg = s / G.W1;
-    if (seg != pseg) {
-        pseg = seg;
-        const int s0 = seg * G.W1, s1 = min(s0 + G.W1, G.Sc);
-        bool mine = true;
-        for (int t = s0 + lane; t < s1; t += 32) {
-            int dx, dy, dz;
-            slot_offsets(G, t, dx, dy, dz);
-            const int ci = R.i + dx, cj = R.j + dy, ck = R.k + dz;
-            if (!smask[t] || ci < 0 || ci >= G.n1 || cj < 0 || cj >= G.n1 || ck < 0 || ck >= G.n1) continue;
-            const long long kr = R.r + dx + (long long)G.n1 * (dy + (long long)G.n1 * dz);
-            mine = mine && wait_flag(rowflag + kr, 1u, err);
-        }
-        if (!__all_sync(0xffffffffu, mine)) return false;
-    }
     int dx, dy, dz;
-    slot_offsets(G, s, dx, dy, dz);
-    const long long kr = R.r + dx + (long long)G.n1 * (dy + (long long)G.n1 * dz);
+    ilu_off(m, dx, dy, dz);
+    return r + dx + (long long)G.n1 * (dy + (long long)G.n1 * dz);
+}
+
+// All lanes copy U row kr into ring buffer dst (16-byte chunks).
+template <typename V>
+__device__ __forceinline__ void ilu_copy_row(const StencilGeo &G, const V *Uv, long long kr, V *dst)
+{
     constexpr int CE = 16 / (int)sizeof(V);
     const V *src = Uv + kr * G.SU;
-    V *dst = ring + (size_t)q * G.SU;
-    for (int c = lane; c < G.SU / CE; c += 32) ilu_cp16(dst + c * CE, src + c * CE);
-    return true;
+    for (int c = (threadIdx.x & 31); c < G.SU / CE; c += 32) ilu_cp16(dst + c * CE, src + c * CE);
 }
 
 template <typename V, int D>
-__global__ void __launch_bounds__(32 * ILU_MAX_WARPS) k_ilu0(StencilGeo G, V *Lv, V *Uv, const int *order,
+__global__ void __launch_bounds__(32 * ILU_MAX_WARPS, 2) k_ilu0(StencilGeo G, V *Lv, V *Uv, const int *order,
                                                             unsigned *rowflag, unsigned *counter, int *err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int S = G.S, Sc = G.Sc, nU = S - Sc, SU = G.SU;
-    const IluSmem Lo = ilu_layout(S, Sc, SU, D, (int)sizeof(V), nw);
-    int *meta = (int *)(smem + Lo.meta);                 // offset (ex,ey,ez) of upper slot u, biased bytes
-    unsigned char *smask = smem + Lo.smask;             // structural flag per slot
+    const IluSmem Lo = ilu_layout(S, SU, D, (int)sizeof(V), nw);
+    int *off = (int *)(smem + Lo.off);           // offset (dx,dy,dz) of every slot, biased bytes
+    unsigned char *smask = smem + Lo.smask;      // structural flag per slot
     V *a = (V *)(smem + Lo.warps + (size_t)wid * Lo.per_warp);
     V *ring = (V *)((unsigned char *)a + al16((size_t)S * sizeof(V)));
-    for (int u = threadIdx.x; u < nU; u += blockDim.x) {
-        int ex, ey, ez;
-        slot_offsets(G, Sc + u, ex, ey, ez);
-        meta[u] = (ex + 128) | ((ey + 128) << 8) | ((ez + 128) << 16);
-    }
     for (int t = threadIdx.x; t < S; t += blockDim.x) {
         int dx, dy, dz;
         slot_offsets(G, t, dx, dy, dz);
+        off[t] = (dx + 128) | ((dy + 128) << 8) | ((dz + 128) << 16);
         smask[t] = structural(G, dx, dy, dz) ? 1 : 0;
     }
     __syncthreads();
@@ -284,42 +267,62 @@ __global__ void __launch_bounds__(32 * ILU_MAX_WARPS) k_ilu0(StencilGeo G, V *Lv
         __syncwarp();
         const V mii = a[Sc];
 
-        // producer cursor: next step whose U row is fetched, and the line whose flags were checked
-        int ps = ilu_next(G, smask, 0, i, j, k), pseg = -1;
-        bool ok = true;
-        const IluRow R{i, j, k, r};
-#pragma unroll
-        for (int q = 0; q < D; ++q) {
-            if (ps < Sc && ok) {
-                ok = ilu_issue<V>(G, R, smask, rowflag, err, Uv, ring, ps, q, pseg) && ok;
-                ps = ilu_next(G, smask, ps + 1, i, j, k);
+        // producer cursor ps: the next step whose U row goes to ring slot pq; bit q of
+        // `ready` says whether slot q holds its step's row (prefetched) or must be
+        // fetched when consumed (its row was not finished at prefetch time)
+        int ps = ilu_next(G, off, smask, 0, i, j, k), pq = 0;
+        unsigned ready = 0;
+        auto prefetch = [&]() {
+            if (ps < Sc) {
+                const long long kr = ilu_row_of(G, r, off[ps]);
+                unsigned f = 0;
+                if (lane == 0) f = ld_acquire(rowflag + kr);
+                f = __shfl_sync(0xffffffffu, f, 0);
+                __syncwarp();
+                if (f) {
+                    ilu_copy_row<V>(G, Uv, kr, ring + (size_t)pq * SU);
+                    ready |= 1u << pq;
+                } else {
+                    ready &= ~(1u << pq);
+                }
+                ps = ilu_next(G, off, smask, ps + 1, i, j, k);
+                pq = (pq + 1 == D) ? 0 : pq + 1;
             }
             ilu_commit();
-        }
-        int cs = ilu_next(G, smask, 0, i, j, k), q = 0;
-        while (cs < Sc && ok) {
+        };
+#pragma unroll 1
+        for (int q = 0; q < D - 1; ++q) prefetch();
+        int cs = ilu_next(G, off, smask, 0, i, j, k), q = 0;
+        bool ok = true;
+        while (cs < Sc) {
+            prefetch();  // step cs + D - 1 into the slot freed by the previous step
             ilu_wait<D - 1>();
+            V *Uk = ring + (size_t)q * SU;
+            if (!(ready >> q & 1u)) {
+                // the row was not finished when prefetched: wait for it, then copy
+                const long long kr = ilu_row_of(G, r, off[cs]);
+                ok = __all_sync(0xffffffffu, wait_flag(rowflag + kr, 1u, err));
+                if (!ok) break;
+                ilu_copy_row<V>(G, Uv, kr, Uk);
+                ilu_commit();
+                ilu_wait<0>();
+            }
             __syncwarp();
-            const V *Uk = ring + (size_t)q * SU;
             const V l = a[cs] * Uk[SU - 1];  // H(r,k) / U(k,k) by the stored reciprocal pivot
             int dx, dy, dz;
-            slot_offsets(G, cs, dx, dy, dz);
+            ilu_off(off[cs], dx, dy, dz);
             for (int u = 1 + lane; u < nU; u += 32) {
-                const int m = meta[u];
-                const int tx = dx + (m & 255) - 128, ty = dy + ((m >> 8) & 255) - 128, tz = dz + ((m >> 16) & 255) - 128;
+                int ex, ey, ez;
+                ilu_off(off[Sc + u], ex, ey, ez);
+                const int tx = dx + ex, ty = dy + ey, tz = dz + ez;
                 if (tx < -G.w || tx > G.w || ty < -G.w || ty > G.w || tz < -G.w || tz > G.w) continue;
                 if (!smask[cs + u]) continue;
                 a[cs + u] -= l * Uk[u];
             }
             __syncwarp();
             if (lane == 0) a[cs] = l;
-            if (ps < Sc && ok) {
-                ok = ilu_issue<V>(G, R, smask, rowflag, err, Uv, ring, ps, q, pseg) && ok;
-                ps = ilu_next(G, smask, ps + 1, i, j, k);
-            }
-            ilu_commit();
             q = (q + 1 == D) ? 0 : q + 1;
-            cs = ilu_next(G, smask, cs + 1, i, j, k);
+            cs = ilu_next(G, off, smask, cs + 1, i, j, k);
         }
         ilu_wait<0>();
         __syncwarp();
@@ -339,10 +342,10 @@ template <typename V, int D>
 static int launch_ilu0_d(lsg_ctx *c, const StencilGeo &G, int nsm, cudaStream_t s)
 {
     const size_t budget = 200 * 1024;
-    const IluSmem one = ilu_layout(G.S, G.Sc, G.SU, D, (int)sizeof(V), 1);
+    const IluSmem one = ilu_layout(G.S, G.SU, D, (int)sizeof(V), 1);
     if (one.total > budget) return LSG_ERR_ARG;  // stencil too wide for a shared-memory row
     int nw = (int)std::min<size_t>(ILU_MAX_WARPS, 1 + (budget - one.total) / one.per_warp);
-    const size_t smem = ilu_layout(G.S, G.Sc, G.SU, D, (int)sizeof(V), nw).total;
+    const size_t smem = ilu_layout(G.S, G.SU, D, (int)sizeof(V), nw).total;
     LSG_CK(cudaFuncSetAttribute(k_ilu0<V, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     LSG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ilu0<V, D>, 32 * nw, smem));
