@@ -391,6 +391,25 @@ def run_native(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_profile_case(args):
+    """One setup + solve of the 2D N=256, T=8 exp-series problem (seeds 1, 2, 3; factors
+    ~0.23 GB, above L2): the small case the ncu captures in profiles/ use."""
+    import torch
+    from paper_2004_13961_gb300 import lsg
+    from paper_2004_13961_gb300 import workloads as W
+    lsg.load()
+    dev = torch.device("cuda", 0)
+    prec = {"n256-fp64": lsg.FP64, "n256-tf32": lsg.MIXED_TF32, "n256-bf16": lsg.MIXED_BF16}[args.profile_case]
+    p = W.random_exp_problem(2, 256, 8, 1, 2, 3)
+    a, b, f = (torch.tensor(p[k], device=dev) for k in ("a", "b", "f"))
+    ctx = lsg.Context(2, 256, 8, a, b, precision=prec)
+    F = ctx.load_vector(f)
+    u, info = ctx.pcg_solve(F, rtol=1e-12 if prec == lsg.FP64 else 1e-10)
+    torch.cuda.synchronize()
+    print(json.dumps(dict(profile_case=args.profile_case, info=info)), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -399,7 +418,12 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--profile-case", choices=["n256-fp64", "n256-tf32", "n256-bf16"], default=None,
+                    help="run one 2D N=256 T=8 setup + solve and exit (the small case of the ncu captures)")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -36,7 +36,6 @@ namespace lsg {
 
 constexpr int SW_MAXB = 8;   // compute warps (lines) per CTA
 constexpr int SW_HELP = 3;   // helper warps: TMA producer, halo loader, publisher
-constexpr int SW_D = 6;      // factor ring depth (rows in flight per line)
 constexpr int SW_KS = 16;    // register-resident slots per lane (1D/2D path)
 
 struct SweepArgs {
@@ -135,7 +134,7 @@ struct SweepSmem {
     int PADL;  // left padding (elements) before position 0
 };
 
-__host__ __device__ inline SweepSmem sweep_layout(int n1, int w, int B, int RL, int vsize, int nslot, int asize)
+__host__ __device__ inline SweepSmem sweep_layout(int n1, int w, int B, int D, int RL, int vsize, int nslot, int asize)
 {
     SweepSmem L;
     const int ce = 16 / asize;                          // elements per 16-byte chunk
@@ -148,12 +147,23 @@ __host__ __device__ inline SweepSmem sweep_layout(int n1, int w, int B, int RL, 
     o = (o + 15) / 16 * 16;
     L.srhs = o;    o += (size_t)B * n1 * asize;
     o = (o + 127) / 128 * 128;
-    L.ring = o;    o += (size_t)B * SW_D * RL * vsize;
+    L.ring = o;    o += (size_t)B * D * RL * vsize;
     o = (o + 7) / 8 * 8;
-    L.mbar = o;    o += (size_t)B * SW_D * 8;
+    L.mbar = o;    o += (size_t)B * D * 8;
     L.meta = o;    o += (size_t)nslot * 4;
     L.total = o;
     return L;
+}
+
+__device__ __forceinline__ int ld_acquire_cta(const volatile int *p)
+{
+    int v;
+    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(smem_u32((const void *)p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_cta(volatile int *p, int v)
+{
+    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(smem_u32((const void *)p)), "r"(v) : "memory");
 }
 
 // Bounded spin until a shared counter reaches `need`: tight polls first (the
@@ -175,15 +185,17 @@ __device__ __forceinline__ bool wait_count(const volatile int *c, int need, cons
     }
 }
 
-template <typename V, typename AT, int DIR>
-__global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid_constant__ SweepArgs A)
+// SW_D: factor ring depth (rows in flight per line), a compile-time constant so
+// that slot indices are cheap; 6, or 4 where the rows are too long for 6
+template <typename V, typename AT, int DIR, int SW_D>
+__global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __grid_constant__ SweepArgs A)
 {
     if (A.done && *A.done) return;
     const StencilGeo G = A.G;
     const int n1 = G.n1, w = G.w, B = A.B, RL = A.RL;
     const int nslot = G.Sc;
     extern __shared__ __align__(128) unsigned char smem[];
-    const SweepSmem Lo = sweep_layout(n1, w, B, RL, (int)sizeof(V), nslot, (int)sizeof(AT));
+    const SweepSmem Lo = sweep_layout(n1, w, B, SW_D, RL, (int)sizeof(V), nslot, (int)sizeof(AT));
     const int RS = Lo.RS, PADL = Lo.PADL;
     int *rowoff = (int *)(smem + Lo.rowoff);
     AT *sy = (AT *)(smem + Lo.sy);
@@ -438,29 +450,33 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
             // wait until position q (sweep order) may be finished and S_{q+1} computed:
             // previous line up to q+w, older lines up to q+w+1, other planes likewise
             auto wait_deps = [&](int q) -> bool {
-                bool good = wait_count(prevc, min(q + w + 1, n1), &s_abort, A.err);
-                if (good && b == 0) good = wait_count(&s_far, min(q + w + 2, n1), &s_abort, A.err);
+                const int need = min(q + w + 1, n1), needfar = min(q + w + 2, n1);
+                // fast path: every lane observes the counters with acquire loads
+                bool fast = ld_acquire_cta(prevc) >= need && (b != 0 || ld_acquire_cta(&s_far) >= needfar);
+                if (vplane >= 0) fast = fast && seen_plane >= (unsigned)needfar;
+                if (__all_sync(0xffffffffu, fast)) return true;
+                bool good = wait_count(prevc, need, &s_abort, A.err);
+                if (good && b == 0) good = wait_count(&s_far, needfar, &s_abort, A.err);
                 if (good && vplane >= 0)
-                    good = wait_flag_cached(A.gprog + plane_real, (unsigned)min(q + w + 2, n1), A.err, &seen_plane);
+                    good = wait_flag_cached(A.gprog + plane_real, (unsigned)needfar, A.err, &seen_plane);
                 good = __all_sync(0xffffffffu, good);
                 __threadfence_block();
                 return good;
             };
-            // S_q: the row's dot product without its two newest terms (all lanes get it)
+            // T_q = r_q - S_q, S_q the row's dot product without its two newest terms
+            // (all lanes get it); lane 0 starts its partial sum at -r_q
             auto stale = [&](int q) -> AT {
                 const int i = DIR > 0 ? q : n1 - 1 - q;
                 const V *row = myring + (size_t)(q % SW_D) * RL + (DIR > 0 ? 0 : 1);
-                AT acc0 = 0, acc1 = 0;
+                AT acc0 = lane == 0 ? -srhs[b * n1 + i] : AT(0);
                 if (regpath) {
                     // a warp-uniform trip count: an FP64 instruction costs its full issue
                     // time even when every lane is predicated off
 #pragma unroll
-                    for (int kk = 0; kk < SW_KS; kk += 2) {
+                    for (int kk = 0; kk < SW_KS; ++kk) {
                         if (kk >= nk) break;
-                        const int t0 = lane + 32 * kk, t1 = t0 + 32;
+                        const int t0 = lane + 32 * kk;
                         if (t0 < nslot && !(freshmask >> kk & 1u)) acc0 += (AT)row[t0] * sy[off[kk] + i];
-                        if (kk + 1 < nk && t1 < nslot && !(freshmask >> (kk + 1) & 1u))
-                            acc1 += (AT)row[t1] * sy[off[kk + 1] + i];
                     }
                 } else {
                     for (int t = lane; t < nslot; t += 32) {
@@ -478,7 +494,7 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
                         acc0 += (AT)row[t] * yv;
                     }
                 }
-                return warp_sum(acc0 + acc1);
+                return -warp_sum(acc0);
             };
             auto wait_row = [&](int q) -> bool {
                 const int slot = q % SW_D;
@@ -490,10 +506,7 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
 
             AT T = 0, yprev = 0;  // T = r_q - S_q of the next position; yprev = y_{q-1}
             if (ok) ok = wait_deps(-1) && wait_row(0);
-            if (ok) {
-                const AT S = stale(0);
-                T = srhs[b * n1 + (DIR > 0 ? 0 : n1 - 1)] - S;
-            }
+            if (ok) T = stale(0);
             int q = 0;
             for (; q < n1 && ok; ++q) {
                 const int i = DIR > 0 ? q : n1 - 1 - q;
@@ -507,8 +520,7 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
                     if (DIR < 0) val = val * (AT)row[RL - 2];  // 1 / U(i,i), stored by the factorisation
                     sy[myrow + i] = val;
                     yprev = val;
-                    __threadfence_block();
-                    s_prog[b] = q + 1;
+                    st_release_cta(&s_prog[b], q + 1);
                 }
                 __syncwarp();
                 if (q + 1 < n1) {
@@ -516,8 +528,7 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
                         ok = false;
                         break;
                     }
-                    const AT S = stale(q + 1);
-                    T = srhs[b * n1 + (DIR > 0 ? q + 1 : n1 - 2 - q)] - S;
+                    T = stale(q + 1);
                 }
             }
             if (live && !ok && lane == 0) s_abort = 1;
@@ -537,18 +548,25 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP)) k_sweep(const __grid
     }
 }
 
-template <typename V, typename AT, int DIR>
+template <typename V, typename AT, int DIR, int D>
 static int launch_sweep(const SweepArgs &A, size_t smem, unsigned grid, cudaStream_t s)
 {
     static size_t attr = 0;  // benign race: setting the attribute twice is harmless
     if (smem > attr) {
-        LSG_CK(cudaFuncSetAttribute(k_sweep<V, AT, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LSG_CK(cudaFuncSetAttribute(k_sweep<V, AT, DIR, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = smem;
     }
     ::lsg::count_launch();
-    k_sweep<V, AT, DIR><<<grid, 32 * (A.B + SW_HELP), smem, s>>>(A);
+    k_sweep<V, AT, DIR, D><<<grid, 32 * (A.B + SW_HELP), smem, s>>>(A);
     LSG_CK(cudaGetLastError());
     return LSG_OK;
+}
+
+template <typename V, typename AT, int DIR>
+static int launch_sweep_d(const SweepArgs &A, int D, size_t smem, unsigned grid, cudaStream_t s)
+{
+    if (D == 6) return launch_sweep<V, AT, DIR, 6>(A, smem, grid, s);
+    return launch_sweep<V, AT, DIR, 4>(A, smem, grid, s);
 }
 
 template <typename V, typename AT>
@@ -564,9 +582,12 @@ static int sweeps(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done, cud
     // clocks), two per sub-partition in FP32; fewer if shared memory runs out
     const size_t budget = 210 * 1024;
     const int RLmax = std::max(g.SL, g.SU);
+    const int vs = (int)sizeof(V), as = (int)sizeof(AT);
     int B = sizeof(AT) == 8 ? 4 : SW_MAXB;
-    while (B > 1 && sweep_layout(g.n1, g.w, B, RLmax, (int)sizeof(V), g.Sc, (int)sizeof(AT)).total > budget) B /= 2;
-    if (sweep_layout(g.n1, g.w, B, RLmax, (int)sizeof(V), g.Sc, (int)sizeof(AT)).total > budget) return LSG_ERR_ARG;
+    while (B > 1 && sweep_layout(g.n1, g.w, B, 4, RLmax, vs, g.Sc, as).total > budget) B /= 2;
+    if (sweep_layout(g.n1, g.w, B, 4, RLmax, vs, g.Sc, as).total > budget) return LSG_ERR_ARG;
+    // factor ring: six rows in flight per line where they fit, else four
+    const int D = sweep_layout(g.n1, g.w, B, 6, RLmax, vs, g.Sc, as).total <= budget ? 6 : 4;
     if (g.w > 31) return LSG_ERR_ARG;  // one halo lane per previous line
     if (B > g.nlines) B = (int)std::max<long long>(1, g.nlines);
     A.B = B;
@@ -584,10 +605,10 @@ static int sweeps(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done, cud
     A.out = ytmp;
     A.gprog = c->prog;
     A.counter = c->counters + 1;
-    size_t smf = sweep_layout(g.n1, g.w, B, g.SL, (int)sizeof(V), g.Sc, (int)sizeof(AT)).total;
+    size_t smf = sweep_layout(g.n1, g.w, B, D, g.SL, vs, g.Sc, as).total;
     int slot;
     LSG_TRY(prof_begin(c, PROF_SWEEP_L, s, &slot));
-    LSG_TRY((launch_sweep<V, AT, 1>(A, smf, grid, s)));
+    LSG_TRY((launch_sweep_d<V, AT, 1>(A, D, smf, grid, s)));
     LSG_TRY(prof_end(c, slot, s));
     // backward: U z = y
     A.F = c->Uv;
@@ -596,9 +617,9 @@ static int sweeps(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done, cud
     A.out = z;
     A.gprog = c->prog + g.nlines;
     A.counter = c->counters + 2;
-    size_t smb = sweep_layout(g.n1, g.w, B, g.SU, (int)sizeof(V), g.Sc, (int)sizeof(AT)).total;
+    size_t smb = sweep_layout(g.n1, g.w, B, D, g.SU, vs, g.Sc, as).total;
     LSG_TRY(prof_begin(c, PROF_SWEEP_U, s, &slot));
-    LSG_TRY((launch_sweep<V, AT, -1>(A, smb, grid, s)));
+    LSG_TRY((launch_sweep_d<V, AT, -1>(A, D, smb, grid, s)));
     LSG_TRY(prof_end(c, slot, s));
     return LSG_OK;
 }
