@@ -197,6 +197,70 @@ def run_reference(args, world, rank):
 
 # --------------------------------------------------------------------------- native (GPU) leg
 
+def run_batched(lsg, W, torch, dev, world, count=256):
+    """Config 4: 256 independent 2D problems, N uniform on {32, 48, ..., 256} (seed 21), T=8,
+    FP64 PCG to 1e-10, all iterations interleaved on the device (lsg_batch_solve).  Timed:
+    setup of every context (ILU(0) included) plus the batched solve."""
+    probs = W.batch_problems(count)
+    dofs = sum((p["N"] - 1) ** 2 for p in probs)
+    dev_in = [(torch.tensor(p["a"], device=dev), torch.tensor(p["b"], device=dev), torch.tensor(p["f"], device=dev))
+              for p in probs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctxs, Fs, us = [], [], []
+    for p, (a, b, f) in zip(probs, dev_in):
+        c = lsg.Context(2, p["N"], p["T"], a, b)
+        Fs.append(c.load_vector(f))
+        us.append(torch.zeros_like(Fs[-1]))
+        ctxs.append(c)
+    t1 = time.perf_counter()
+    st, infos = lsg.batch_solve(ctxs, Fs, us, rtol=1e-10)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    for c in ctxs:
+        c.close()
+    ok = sum(1 for i in infos if i["status"] == 0)
+    total = max_over_ranks(t2 - t0, world)
+    return dict(problems=count, converged=ok, dof_total=dofs, rtol=1e-10, precision="fp64",
+                setup_s=t1 - t0, solve_s=t2 - t1, solves_s=world * count / total,
+                gdof_s=world * dofs / total / 1e9, iters_mean=float(np.mean([i["iters"] for i in infos])),
+                note="per-problem streams with device-resident PCG state; setup included")
+
+
+def run_serving(lsg, W, world, count=48):
+    """A bounded sample of config 5: Poisson arrivals (seed 31), 70% 2D with N log-uniform in
+    [64, 512], 30% 3D with N uniform in [24, 40], T in {4, 8}, a = exp(g) with sigma in
+    [0.5, 2.3]; mixed TF32 refined to 1e-10; HBM-admitted (64 GB budget, 4 slots).  Latency is
+    submit -> solution in host memory."""
+    reqs = W.serving_stream(count, seed=31, rate_hz=20.0, n2d=(64, 512), n3d=(24, 40))
+    data = []
+    for r in reqs:
+        p = W.random_exp_problem(r["d"], r["N"], r["T"], r["seed"], r["seed"] + 1, r["seed"] + 2, sigma=r["sigma"])
+        data.append((r, p))
+    srv = lsg.Server(64 << 30, max_inflight=4)
+    t0 = time.perf_counter()
+    for i, (r, p) in enumerate(data):
+        delay = r["arrival_s"] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        srv.submit(i, r["d"], r["N"], r["T"], p["a"], p["b"], p["f"], precision=lsg.MIXED_TF32, rtol=1e-10)
+    srv.drain()
+    t1 = time.perf_counter()
+    res = srv.poll(count + 8)
+    srv.close()
+    lat = np.array([x["latency_ms"] for x in res if x["info"]["status"] == 0])
+    st = [x["info"]["status"] for x in res]
+    out = dict(requests=count, completed=int((np.array(st) == 0).sum()),
+               ilu_breakdown=int((np.array(st) == lsg.ERR_ILU_BREAKDOWN).sum()),
+               other_errors=int(sum(1 for v in st if v not in (0, lsg.ERR_ILU_BREAKDOWN))),
+               wall_s=t1 - t0, solves_s=world * len(lat) / max_over_ranks(t1 - t0, world),
+               precision="mixed-tf32", rtol=1e-10, arrival_rate_hz=20.0,
+               sample="48 requests of the config-5 mix, N capped at 512 (2D) and 40 (3D)")
+    if len(lat):
+        out.update(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)))
+    return out
+
+
 def run_native(args, world, rank, local):
     import torch
     from paper_2004_13961_gb300 import lsg
@@ -325,11 +389,15 @@ def run_native(args, world, rank, local):
             res = {}
 
             def mstep():
-                c3 = lsg.Context(d, N, T, a, b, Q=Q, precision=prec)
+                c3 = lsg.Context(d, N, T, a, b, Q=Q, precision=prec, profile=True)
                 c3.load_vector(f, F)
                 um.zero_()
                 _, inf = c3.pcg_solve(F, um, rtol=1e-10)
                 res["info"] = inf
+                res["stages"] = dict(ilu_ms=c3.query(lsg.Q_ILU_US) / 1e3,
+                                     sweeps_ms=(c3.query(lsg.Q_SWEEP_L_US) + c3.query(lsg.Q_SWEEP_U_US)) / 1e3,
+                                     kx_tensor_core_ms=c3.query(lsg.Q_KX_LO_US) / 1e3,
+                                     kx_tensor_core_calls=c3.query(lsg.Q_KX_LO_CALLS))
                 c3.close()
 
             for _ in range(2):
@@ -349,8 +417,8 @@ def run_native(args, world, rank, local):
             mixed[name] = dict(solves_s=world * 1e3 / max_over_ranks(float(np.mean(ms)), world),
                                ms_per_solve=float(np.mean(ms)), rtol=1e-10, relres_true=inf["relres_true"],
                                inner_iters=inf["iters"], refinements=inf["outer_iters"],
-                               rel_err_vs_fp64_gpu=err,
-                               transforms="FP32 CUDA cores (tensor-core transforms not wired yet)")
+                               rel_err_vs_fp64_gpu=err, stages_last_solve=res["stages"],
+                               transforms=f"tcgen05 tensor cores, {name.upper()} operands split hi+lo (3 MMAs), FP32 accumulation")
 
     # ---- e2e: host buffers through the C ABI, copies inside the timed region ----
     ha, hb, hf = p["a"].copy(), p["b"].copy(), p["f"].copy()
@@ -371,6 +439,9 @@ def run_native(args, world, rank, local):
     e2e = dict(value=e2e_val, unit="solves/s", h2d_bytes_per_step=3 * nq * 8 + 2 * n * 8,
                d2h_bytes_per_step=2 * n * 8)
 
+    batched = None if args.no_batch else run_batched(lsg, W, torch, dev, world)
+    serving = None if args.no_serving else run_serving(lsg, W, world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = oracle_sample(p, iters)
@@ -387,6 +458,7 @@ def run_native(args, world, rank, local):
                         parallelism=f"replicas x{world}"),
             kx_gdof_s=n / (t_kx * 1e-3) / 1e9, kx_ms=t_kx, minv_ms=t_minv, pcg_iters=iters,
             relres_true=info["relres_true"], breakdown_ms_per_solve=per_solve, mixed=mixed or None,
+            batched=batched, serving=serving,
             roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clocks)
         print(json.dumps(line), flush=True)
 
@@ -418,6 +490,8 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--profile-case", choices=["n256-fp64", "n256-tf32", "n256-bf16"], default=None,
                     help="run one 2D N=256 T=8 setup + solve and exit (the small case of the ncu captures)")
     args = ap.parse_args()

@@ -577,13 +577,13 @@ static int sweeps(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done, cud
     A.G = sgeo(g);
     A.done = done;
     A.err = c->err;
-    // lines per CTA: one per SM sub-partition when the dot products run in FP64
-    // (an FP64 warp instruction occupies its sub-partition's FP64 unit for ~64
-    // clocks), two per sub-partition in FP32; fewer if shared memory runs out
+    // lines per CTA: one per SM sub-partition (an FP64 warp instruction occupies its
+    // sub-partition's FP64 unit for ~64 clocks; in FP32 a second line per
+    // sub-partition measured slower too); fewer if shared memory runs out
     const size_t budget = 210 * 1024;
     const int RLmax = std::max(g.SL, g.SU);
     const int vs = (int)sizeof(V), as = (int)sizeof(AT);
-    int B = sizeof(AT) == 8 ? 4 : SW_MAXB;
+    int B = 4;
     while (B > 1 && sweep_layout(g.n1, g.w, B, 4, RLmax, vs, g.Sc, as).total > budget) B /= 2;
     if (sweep_layout(g.n1, g.w, B, 4, RLmax, vs, g.Sc, as).total > budget) return LSG_ERR_ARG;
     // factor ring: six rows in flight per line where they fit, else four
