@@ -479,19 +479,30 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
                         if (t0 < nslot && !(freshmask >> kk & 1u)) acc0 += (AT)row[t0] * sy[off[kk] + i];
                     }
                 } else {
-                    for (int t = lane; t < nslot; t += 32) {
-                        if (t == f_own || t == f_prev) continue;
-                        const unsigned m = meta[t];
-                        const int dx = (int)(m & 255u) - 128, dy = (int)((m >> 8) & 255u) - 128,
-                                  dz = (int)((m >> 16) & 255u) - 128;
-                        const int ci = i + dx, cj = j + dy, ck = k + dz;
-                        if (ci < 0 || ci >= n1 || cj < 0 || cj >= n1 || ck < 0 || ck >= n1) continue;
-                        AT yv;
-                        if (dz == 0)
-                            yv = sy[rowoff[b + w + DIR * dy] + ci];
-                        else
-                            yv = __ldcg(out + ci + (long long)n1 * (cj + (long long)n1 * ck));
-                        acc0 += (AT)row[t] * yv;
+                    // eight slots per lane at a time: all their loads are issued before the
+                    // first multiply-add, so the L2 latency of the other planes' values is
+                    // paid once per group rather than once per slot
+                    constexpr int G8 = 8;
+                    for (int t0 = lane; t0 < nslot; t0 += 32 * G8) {
+                        AT yv[G8];
+                        V fv[G8];
+#pragma unroll
+                        for (int u = 0; u < G8; ++u) {
+                            const int t = t0 + 32 * u;
+                            yv[u] = AT(0);
+                            fv[u] = V(0);
+                            if (t >= nslot || t == f_own || t == f_prev) continue;
+                            const unsigned m = meta[t];
+                            const int dx = (int)(m & 255u) - 128, dy = (int)((m >> 8) & 255u) - 128,
+                                      dz = (int)((m >> 16) & 255u) - 128;
+                            const int ci = i + dx, cj = j + dy, ck = k + dz;
+                            if (ci < 0 || ci >= n1 || cj < 0 || cj >= n1 || ck < 0 || ck >= n1) continue;
+                            fv[u] = row[t];
+                            yv[u] = dz == 0 ? sy[rowoff[b + w + DIR * dy] + ci]
+                                            : __ldcg(out + ci + (long long)n1 * (cj + (long long)n1 * ck));
+                        }
+#pragma unroll
+                        for (int u = 0; u < G8; ++u) acc0 += (AT)fv[u] * yv[u];
                     }
                 }
                 return -warp_sum(acc0);
@@ -504,20 +515,32 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
                 return __all_sync(0xffffffffu, good);
             };
 
-            AT T = 0, yprev = 0;  // T = r_q - S_q of the next position; yprev = y_{q-1}
+            // T = r_q - S_q of the next position; yprev = y_{q-1}; lo, lp, ri: the factors of
+            // the two newest terms and 1 / U(i,i) of the next position (read ahead by lane 0)
+            AT T = 0, yprev = 0, lo = 0, lp = 0, ri = 1;
+            auto fresh_factors = [&](int q) {
+                if (lane == 0) {
+                    const V *row = myring + (size_t)(q % SW_D) * RL + (DIR > 0 ? 0 : 1);
+                    lo = (AT)row[f_own];
+                    lp = f_prev >= 0 ? (AT)row[f_prev] : AT(0);
+                    if (DIR < 0) ri = (AT)row[RL - 2];  // 1 / U(i,i), stored by the factorisation
+                }
+            };
             if (ok) ok = wait_deps(-1) && wait_row(0);
-            if (ok) T = stale(0);
+            if (ok) {
+                T = stale(0);
+                fresh_factors(0);
+            }
             int q = 0;
             for (; q < n1 && ok; ++q) {
                 const int i = DIR > 0 ? q : n1 - 1 - q;
+                // the own-line term is known before the previous line's value arrives
+                const AT t = T - lo * yprev;
                 ok = wait_deps(q);
                 if (!ok) break;
                 if (lane == 0) {
-                    const V *row = myring + (size_t)(q % SW_D) * RL + (DIR > 0 ? 0 : 1);
-                    AT val = T;
-                    if (f_prev >= 0) val -= (AT)row[f_prev] * sy[prevoff + i];
-                    val -= (AT)row[f_own] * yprev;
-                    if (DIR < 0) val = val * (AT)row[RL - 2];  // 1 / U(i,i), stored by the factorisation
+                    AT val = t - lp * sy[prevoff + i];
+                    if (DIR < 0) val = val * ri;
                     sy[myrow + i] = val;
                     yprev = val;
                     st_release_cta(&s_prog[b], q + 1);
@@ -529,6 +552,7 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
                         break;
                     }
                     T = stale(q + 1);
+                    fresh_factors(q + 1);
                 }
             }
             if (live && !ok && lane == 0) s_abort = 1;
