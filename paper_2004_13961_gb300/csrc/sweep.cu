@@ -319,7 +319,9 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
             // positions of that line are finished (progress acquired from global
             // memory), waits for the copies, then publishes how far the nearest line
             // and the older ones are staged
-            const bool hl = lane < w && (v0 - 1 - lane) >= 0 && !aborted;
+            // a line of another plane (3D) is no neighbour of the band's first line: it is
+            // neither staged nor waited for (its slots carry zero factors)
+            const bool hl = lane < w && (v0 - 1 - lane) >= 0 && (v0 - 1 - lane) / n1 == v0 / n1 && !aborted;
             const long long hv = v0 - 1 - lane;
             const long long hline = hl ? (DIR > 0 ? hv : G.nlines - 1 - hv) : 0;
             long long hchunk = 0;
@@ -449,8 +451,11 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
 
             // wait until position q (sweep order) may be finished and S_{q+1} computed:
             // previous line up to q+w, older lines up to q+w+1, other planes likewise
+            // the first line of a plane (3D) has no previous line in its plane: the line
+            // before it in sweep order is the last of the previous plane, no neighbour
+            const bool needprev = !(G.d == 3 && jv == 0);
             auto wait_deps = [&](int q) -> bool {
-                const int need = min(q + w + 1, n1), needfar = min(q + w + 2, n1);
+                const int need = needprev ? min(q + w + 1, n1) : 0, needfar = min(q + w + 2, n1);
                 // fast path: every lane observes the counters with acquire loads
                 bool fast = ld_acquire_cta(prevc) >= need && (b != 0 || ld_acquire_cta(&s_far) >= needfar);
                 if (vplane >= 0) fast = fast && seen_plane >= (unsigned)needfar;
@@ -479,15 +484,16 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
                         if (t0 < nslot && !(freshmask >> kk & 1u)) acc0 += (AT)row[t0] * sy[off[kk] + i];
                     }
                 } else {
-                    // eight slots per lane at a time: all their loads are issued before the
+                    // 8 (FP64) or 12 slots per lane at a time: all their loads are issued before the
                     // first multiply-add, so the L2 latency of the other planes' values is
                     // paid once per group rather than once per slot
-                    constexpr int G8 = 8;
+                    constexpr int G8 = sizeof(AT) == 8 ? 8 : 12;
                     for (int t0 = lane; t0 < nslot; t0 += 32 * G8) {
                         AT yv[G8];
                         V fv[G8];
 #pragma unroll
                         for (int u = 0; u < G8; ++u) {
+                            if ((t0 - lane) + 32 * u >= nslot) break;  // warp-uniform
                             const int t = t0 + 32 * u;
                             yv[u] = AT(0);
                             fv[u] = V(0);
@@ -502,7 +508,10 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
                                             : __ldcg(out + ci + (long long)n1 * (cj + (long long)n1 * ck));
                         }
 #pragma unroll
-                        for (int u = 0; u < G8; ++u) acc0 += (AT)fv[u] * yv[u];
+                        for (int u = 0; u < G8; ++u) {
+                            if ((t0 - lane) + 32 * u >= nslot) break;  // warp-uniform: no idle FP64 issue
+                            acc0 += (AT)fv[u] * yv[u];
+                        }
                     }
                 }
                 return -warp_sum(acc0);
