@@ -311,11 +311,39 @@ __global__ void __launch_bounds__(32 * ILU_MAX_WARPS, 2) k_ilu0(StencilGeo G, V 
             const V l = a[cs] * Uk[SU - 1];  // H(r,k) / U(k,k) by the stored reciprocal pivot
             int dx, dy, dz;
             ilu_off(off[cs], dx, dy, dz);
-            for (int u = 1 + lane; u < nU; u += 32) {
+            // Only the upper offsets e of row k whose target d+e stays in the box are
+            // enumerated, packed over the lanes: per axis the valid e form a range, so the
+            // targets are the runs (ez, ey, ex in [exlo, exhi]), with the half-plane ez = 0
+            // restricted to ey > 0, or ey = 0 and ex > 0 (e above the diagonal).
+            const int wy = G.d >= 2 ? G.w : 0, wz = G.d == 3 ? G.w : 0;
+            const int exlo = max(-G.w, -G.w - dx), exhi = min(G.w, G.w - dx);
+            const int eylo = max(-wy, -wy - dy), eyhi = min(wy, wy - dy);
+            const int Lx = exhi - exlo + 1, Ly = eyhi - eylo + 1, Lz = min(wz, wz - dz) + 1;
+            const int ex0 = max(1, exlo);
+            const int len0 = max(0, exhi - ex0 + 1);     // ez = 0, ey = 0
+            const int n0 = len0 + max(0, eyhi) * Lx;      // ez = 0, ey in [1, eyhi]
+            const int cnt = n0 + (Lz - 1) * Ly * Lx;      // ez in [1, Lz)
+            const float ilx = 1.0f / (float)Lx, ilyx = 1.0f / (float)(Ly * Lx);
+            const int sbase = G.w + G.W1 * (wy + G.W1 * wz) - Sc;  // slot(e) - Sc = ex + W1 ey + W1^2 ez + sbase
+            for (int f = lane; f < cnt; f += 32) {
                 int ex, ey, ez;
-                ilu_off(off[Sc + u], ex, ey, ez);
-                const int tx = dx + ex, ty = dy + ey, tz = dz + ez;
-                if (tx < -G.w || tx > G.w || ty < -G.w || ty > G.w || tz < -G.w || tz > G.w) continue;
+                if (f < len0) {
+                    ez = 0;
+                    ey = 0;
+                    ex = ex0 + f;
+                } else if (f < n0) {
+                    const int g = f - len0, qy = (int)(((float)g + 0.5f) * ilx);
+                    ez = 0;
+                    ey = 1 + qy;
+                    ex = exlo + (g - qy * Lx);
+                } else {
+                    const int h = f - n0, qz = (int)(((float)h + 0.5f) * ilyx);
+                    const int rem = h - qz * Ly * Lx, qy = (int)(((float)rem + 0.5f) * ilx);
+                    ez = 1 + qz;
+                    ey = eylo + qy;
+                    ex = exlo + (rem - qy * Lx);
+                }
+                const int u = ex + G.W1 * (ey + G.W1 * ez) + sbase;
                 if (!smask[cs + u]) continue;
                 a[cs + u] -= l * Uk[u];
             }
