@@ -200,10 +200,12 @@ def run_reference(args, world, rank):
 
 # --------------------------------------------------------------------------- native (GPU) leg
 
-def run_batched(lsg, W, torch, dev, world, count=256):
+def run_batched(lsg, W, torch, dev, world, count=256, precision=None):
     """Config 4: 256 independent 2D problems, N uniform on {32, 48, ..., 256} (seed 21), T=8,
-    FP64 PCG to 1e-10, all iterations interleaved on the device (lsg_batch_solve).  Timed:
-    setup of every context (ILU(0) included) plus the batched solve."""
+    PCG to 1e-10 through lsg_batch_solve (FP64: all iterations interleaved on the device;
+    mixed: concurrent refined solves).  Timed: setup of every context (ILU(0) included) plus
+    the batched solve."""
+    precision = lsg.FP64 if precision is None else precision
     probs = W.batch_problems(count)
     dofs = sum((p["N"] - 1) ** 2 for p in probs)
     dev_in = [(torch.tensor(p["a"], device=dev), torch.tensor(p["b"], device=dev), torch.tensor(p["f"], device=dev))
@@ -213,7 +215,7 @@ def run_batched(lsg, W, torch, dev, world, count=256):
     ctxs, Fs, us = [], [], []
     breakdowns = 0
     for p, (a, b, f) in zip(probs, dev_in):
-        c = lsg.Context(2, p["N"], p["T"], a, b, allow_breakdown=True)
+        c = lsg.Context(2, p["N"], p["T"], a, b, allow_breakdown=True, precision=precision)
         if c.status == lsg.ERR_ILU_BREAKDOWN:  # ILU(0) of this M does not exist: counted, not solved
             breakdowns += 1
             c.close()
@@ -230,18 +232,19 @@ def run_batched(lsg, W, torch, dev, world, count=256):
     ok = sum(1 for i in infos if i["status"] == 0)
     total = max_over_ranks(t2 - t0, world)
     return dict(problems=count, converged=ok, ilu_breakdown=breakdowns, dof_total=dofs, rtol=1e-10,
-                precision="fp64",
+                precision={lsg.FP64: "fp64", lsg.MIXED_TF32: "mixed-tf32", lsg.MIXED_BF16: "mixed-bf16"}[precision],
                 setup_s=t1 - t0, solve_s=t2 - t1, solves_s=world * ok / total,
                 gdof_s=world * dofs / total / 1e9, iters_mean=float(np.mean([i["iters"] for i in infos])),
-                note="per-problem streams with device-resident PCG state; setup included")
+                note=("per-problem streams with device-resident PCG state" if precision == lsg.FP64 else
+                      "concurrent refined solves, 8 host threads / streams") + "; setup included")
 
 
-def run_serving(lsg, W, world, count=48):
+def run_serving(lsg, W, world, count=32, rate=4.0):
     """A bounded sample of config 5: Poisson arrivals (seed 31), 70% 2D with N log-uniform in
     [64, 512], 30% 3D with N uniform in [24, 40], T in {4, 8}, a = exp(g) with sigma in
     [0.5, 2.3]; mixed TF32 refined to 1e-10; HBM-admitted (64 GB budget, 4 slots).  Latency is
-    submit -> solution in host memory."""
-    reqs = W.serving_stream(count, seed=31, rate_hz=20.0, n2d=(64, 512), n3d=(24, 40))
+    submit -> solution in host memory; requests whose ILU(0) breaks down are counted."""
+    reqs = W.serving_stream(count, seed=31, rate_hz=rate, n2d=(64, 512), n3d=(24, 40))
     data = []
     for r in reqs:
         p = W.random_exp_problem(r["d"], r["N"], r["T"], r["seed"], r["seed"] + 1, r["seed"] + 2, sigma=r["sigma"])
@@ -259,12 +262,20 @@ def run_serving(lsg, W, world, count=48):
     srv.close()
     lat = np.array([x["latency_ms"] for x in res if x["info"]["status"] == 0])
     st = [x["info"]["status"] for x in res]
+    by_class = {}
+    for dd in (2, 3):
+        l = np.array([x["latency_ms"] for x in res if x["info"]["status"] == 0 and data[x["id"]][0]["d"] == dd])
+        n_req = sum(1 for r, _ in data if r["d"] == dd)
+        c = dict(requests=n_req, completed=int(len(l)))
+        if len(l):
+            c.update(p50_ms=float(np.percentile(l, 50)), p99_ms=float(np.percentile(l, 99)))
+        by_class[f"{dd}d"] = c
     out = dict(requests=count, completed=int((np.array(st) == 0).sum()),
                ilu_breakdown=int((np.array(st) == lsg.ERR_ILU_BREAKDOWN).sum()),
                other_errors=int(sum(1 for v in st if v not in (0, lsg.ERR_ILU_BREAKDOWN))),
                wall_s=t1 - t0, solves_s=world * len(lat) / max_over_ranks(t1 - t0, world),
-               precision="mixed-tf32", rtol=1e-10, arrival_rate_hz=20.0,
-               sample="48 requests of the config-5 mix, N capped at 512 (2D) and 40 (3D)")
+               precision="mixed-tf32", rtol=1e-10, arrival_rate_hz=rate, by_class=by_class,
+               sample=f"{count} requests of the config-5 mix at {rate} Hz, N capped at 512 (2D) and 40 (3D)")
     if len(lat):
         out.update(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)))
     return out
@@ -452,7 +463,9 @@ def run_native(args, world, rank, local):
     e2e = dict(value=e2e_val, unit="solves/s", h2d_bytes_per_step=3 * nq * 8 + 2 * n * 8,
                d2h_bytes_per_step=2 * n * 8)
 
-    batched = None if args.no_batch else run_batched(lsg, W, torch, dev, world)
+    batched = None if args.no_batch else dict(
+        fp64=run_batched(lsg, W, torch, dev, world),
+        mixed_tf32=run_batched(lsg, W, torch, dev, world, precision=lsg.MIXED_TF32))
     serving = None if args.no_serving else run_serving(lsg, W, world)
 
     cpu = None

@@ -212,7 +212,9 @@ int lsg_destroy(lsg_ctx *ctx);
 /* Batched PCG over `count` independent contexts (uneven sizes allowed):
  * the iterations of all problems are interleaved on the device, each problem
  * stopping at its own tolerance.  F[i], u[i] as in lsg_pcg_solve; infos may
- * be NULL.  Synchronises `stream`. */
+ * be NULL.  When any context is mixed-precision, the problems run as
+ * concurrent lsg_pcg_solve calls (a few host threads, one stream each).
+ * Returns the first non-OK status.  Synchronises `stream`. */
 int lsg_batch_solve(int count, lsg_ctx *const *ctxs, const double *const *F, double *const *u,
                     double rtol, int kmax, lsg_info *infos, lsg_stream_t stream);
 

@@ -1,13 +1,52 @@
 // batch.cu -- batched PCG over many independent problems (uneven sizes).
 // Every problem runs Algorithm 1 on its own stream; the host advances all runs
 // without blocking on any one of them, so the kernels of different problems
-// overlap on the device and each problem stops at its own tolerance.
+// overlap on the device and each problem stops at its own tolerance.  Mixed-
+// precision contexts (FP64 refinement around an FP32 inner PCG, whose steps
+// need host decisions between refinements) run as concurrent solves, one host
+// thread and stream each, a bounded number at a time.
+#include <algorithm>
+#include <atomic>
 #include <thread>
 #include <vector>
 
 #include "lsg_internal.cuh"
 
 using namespace lsg;
+
+// Concurrent whole solves (lsg_pcg_solve) on per-thread streams, at most
+// kConc at a time; the caller's stream is ordered before and after them.
+static int batch_concurrent(int count, lsg_ctx *const *ctxs, const double *const *F, double *const *u, double rtol,
+                            int kmax, lsg_info *infos, cudaStream_t s0)
+{
+    constexpr int kConc = 8;
+    int dev = 0;
+    LSG_CK(cudaGetDevice(&dev));
+    LSG_CK(cudaStreamSynchronize(s0));
+    std::vector<int> status(count, LSG_OK);
+    std::vector<lsg_info> inf(count);
+    std::atomic<int> next{0};
+    auto work = [&]() {
+        cudaSetDevice(dev);
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            for (int i; (i = next.fetch_add(1)) < count;) status[i] = LSG_ERR_CUDA;
+            return;
+        }
+        for (int i; (i = next.fetch_add(1)) < count;)
+            status[i] = lsg_pcg_solve(ctxs[i], F[i], u[i], rtol, kmax, &inf[i], (lsg_stream_t)s);
+        cudaStreamDestroy(s);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 0; t < std::min(kConc, count); ++t) pool.emplace_back(work);
+    for (auto &t : pool) t.join();
+    int st = LSG_OK;
+    for (int i = 0; i < count; ++i) {
+        if (infos) infos[i] = inf[i];
+        if (status[i] != LSG_OK && st == LSG_OK) st = status[i];
+    }
+    return st;
+}
 
 extern "C" int lsg_batch_solve(int count, lsg_ctx *const *ctxs, const double *const *F, double *const *u,
                                double rtol, int kmax, lsg_info *infos, lsg_stream_t stream)
@@ -17,6 +56,9 @@ extern "C" int lsg_batch_solve(int count, lsg_ctx *const *ctxs, const double *co
     for (int i = 0; i < count; ++i)
         if (!ctxs[i] || !F[i] || !u[i]) return LSG_ERR_ARG;
     cudaStream_t s0 = (cudaStream_t)stream;
+    bool mixed = false;
+    for (int i = 0; i < count; ++i) mixed = mixed || ctxs[i]->precision != LSG_FP64;
+    if (mixed) return batch_concurrent(count, ctxs, F, u, rtol, kmax, infos, s0);
     std::vector<cudaStream_t> st(count, nullptr);
     std::vector<PcgRun> runs(count);
     std::vector<bool> fin(count, false), hostu(count, false);

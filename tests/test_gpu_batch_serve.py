@@ -109,3 +109,24 @@ def test_serving_rejects_request_over_budget(lsg):
     srv = lsg.Server(fp // 2, max_inflight=1)
     assert srv.submit(0, p["d"], p["N"], p["T"], p["a"], p["b"], p["f"], Q=p["Q"]) == lsg.ERR_NOMEM
     srv.close()
+
+
+def test_batch_mixed_equals_alone(lsg):
+    probs = _problems()[:4]
+    ctxs, Fs, alone = [], [], []
+    for p in probs:
+        c = lsg.Context(p["d"], p["N"], p["T"], torch.tensor(p["a"], device=DEV), torch.tensor(p["b"], device=DEV),
+                        precision=lsg.MIXED_TF32)
+        F = c.load_vector(torch.tensor(p["f"], device=DEV))
+        u1, i1 = c.pcg_solve(F, rtol=1e-10)
+        alone.append((u1.cpu().numpy(), i1))
+        ctxs.append(c)
+        Fs.append(F)
+    us = [torch.zeros_like(F) for F in Fs]
+    st, infos = lsg.batch_solve(ctxs, Fs, us, rtol=1e-10)
+    assert st == lsg.OK
+    for c, u, info, (ua, ia) in zip(ctxs, us, infos, alone):
+        assert info["status"] == lsg.OK and info["relres_true"] <= 1e-10
+        assert info["iters"] == ia["iters"] and info["outer_iters"] == ia["outer_iters"]
+        assert rel(u.cpu().numpy(), ua) < 1e-12
+        c.close()
