@@ -185,7 +185,8 @@ int lsg_apply_A_lowp(lsg_ctx *ctx, const float *x, float *y, lsg_stream_t stream
 
 /* z = U^{-1} L^{-1} r: the one-step ILU(0) preconditioner solve (Sec. 4.2,
  * Algorithms 3 and 4).  r, z: n doubles; z must not alias r.  Mixed-precision
- * contexts sweep FP32 factors with FP32 accumulation. */
+ * contexts hold FP32 factors; this call sweeps them with FP64 accumulation
+ * (their inner PCG sweeps FP32 vectors in FP32). */
 int lsg_apply_Minv(lsg_ctx *ctx, const double *r, double *z, lsg_stream_t stream);
 
 /* PCG (Algorithm 1) on K u = F with the ILU(0) preconditioner.

@@ -8,27 +8,31 @@
 // be finished once the previous line has finished position i+w.
 //
 // Kernel design (GB300).  A CTA owns a band of B consecutive lines, one
-// compute warp per line, and runs in lockstep ticks: at tick t, line b
-// finishes its row t - (w+1) b.  Every value that row needs was finished at a
-// tick <= t-1 (own line: previous position; line b-1: position + w; older
-// lines and the halo further back), so a tick is a dot product per warp, a
-// warp reduction and one named barrier -- no waits between the lines of a
-// band.  All data movement is done by three helper warps, off the tick's
-// critical path:
+// compute warp per line.  A line warp advances as soon as its inputs exist:
+// it waits only for its predecessor's progress counter in shared memory (the
+// halo loader publishes separate counts for the line before the band and the
+// older halo lines).  Each row's dot product is split: the stale part -- every
+// term but the two newest dependencies (the previous position of the line and
+// position +w of the previous line) -- is computed one position ahead, off the
+// critical path; finishing a row is then two multiply-adds and, backward, a
+// multiply by the reciprocal pivot the factorisation stored.  All data
+// movement is done by three helper warps:
 //   * a TMA producer streams factor rows into a per-line ring in shared memory
 //     with bulk copies (cp.async.bulk) that complete on mbarriers, D rows ahead
-//     of the tick that consumes them;
+//     of the row that reads them;
 //   * a halo loader stages the w lines before the band (finished by the
 //     previous band) into shared memory with 16-byte cp.async copies as soon
-//     as their progress words allow, and publishes how far the halo is ready;
+//     as their progress words allow, and publishes how far they are staged;
 //   * a publisher copies finished values to global memory and releases
 //     per-line progress words.
-// The compute warps keep their stencil offsets in registers and read padded,
-// zero-initialised row buffers, so the 1D/2D dot product has no branches: a
-// slot outside the grid carries an exact-zero factor.  In 3D, neighbours in
-// other planes are read from global memory after the plane's progress word is
-// acquired.  Bands are claimed in sweep order, so a CTA only waits for lines
-// claimed earlier by a running CTA; every wait is bounded and reports
+// The 1D/2D line warps keep their stencil offsets in registers and read padded,
+// zero-initialised row buffers, so the dot product has no branches: a slot
+// outside the grid carries an exact-zero factor.  In 3D, neighbours in other
+// planes are read from global memory (in groups of slots per lane) after the
+// plane's progress word is acquired, and a plane's first line does not wait
+// for the line before it in sweep order (the last line of the previous plane,
+// no neighbour).  Bands are claimed in sweep order, so a CTA only waits for
+// lines claimed earlier by a running CTA; every wait is bounded and reports
 // LSG_ERR_TIMEOUT through the device error word.
 #include "stencil.cuh"
 
