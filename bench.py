@@ -239,10 +239,11 @@ def run_batched(lsg, W, torch, dev, world, count=256, precision=None):
                       "concurrent refined solves, 8 host threads / streams") + "; setup included")
 
 
-def run_serving(lsg, W, world, count=32, rate=4.0):
+def run_serving(lsg, W, world, count=32, rate=4.0, precision=None):
     """A bounded sample of config 5: Poisson arrivals (seed 31), 70% 2D with N log-uniform in
     [64, 512], 30% 3D with N uniform in [24, 40], T in {4, 8}, a = exp(g) with sigma in
-    [0.5, 2.3]; mixed TF32 refined to 1e-10; HBM-admitted (64 GB budget, 4 slots).  Latency is
+    [0.5, 2.3]; refined to 1e-10 (mixed TF32, or plain FP64 PCG for comparison); HBM-admitted
+    (64 GB budget, 4 slots, smallest footprint first).  Latency is
     submit -> solution in host memory; requests whose ILU(0) breaks down are counted."""
     reqs = W.serving_stream(count, seed=31, rate_hz=rate, n2d=(64, 512), n3d=(24, 40))
     data = []
@@ -255,7 +256,7 @@ def run_serving(lsg, W, world, count=32, rate=4.0):
         delay = r["arrival_s"] - (time.perf_counter() - t0)
         if delay > 0:
             time.sleep(delay)
-        srv.submit(i, r["d"], r["N"], r["T"], p["a"], p["b"], p["f"], precision=lsg.MIXED_TF32, rtol=1e-10)
+        srv.submit(i, r["d"], r["N"], r["T"], p["a"], p["b"], p["f"], precision=precision, rtol=1e-10)
     srv.drain()
     t1 = time.perf_counter()
     res = srv.poll(count + 8)
@@ -274,7 +275,8 @@ def run_serving(lsg, W, world, count=32, rate=4.0):
                ilu_breakdown=int((np.array(st) == lsg.ERR_ILU_BREAKDOWN).sum()),
                other_errors=int(sum(1 for v in st if v not in (0, lsg.ERR_ILU_BREAKDOWN))),
                wall_s=t1 - t0, solves_s=world * len(lat) / max_over_ranks(t1 - t0, world),
-               precision="mixed-tf32", rtol=1e-10, arrival_rate_hz=rate, by_class=by_class,
+               precision="mixed-tf32" if precision == lsg.MIXED_TF32 else "fp64", rtol=1e-10,
+               arrival_rate_hz=rate, by_class=by_class,
                sample=f"{count} requests of the config-5 mix at {rate} Hz, N capped at 512 (2D) and 40 (3D)")
     if len(lat):
         out.update(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)))
@@ -466,7 +468,8 @@ def run_native(args, world, rank, local):
     batched = None if args.no_batch else dict(
         fp64=run_batched(lsg, W, torch, dev, world),
         mixed_tf32=run_batched(lsg, W, torch, dev, world, precision=lsg.MIXED_TF32))
-    serving = None if args.no_serving else run_serving(lsg, W, world)
+    serving = None if args.no_serving else dict(mixed_tf32=run_serving(lsg, W, world, precision=lsg.MIXED_TF32),
+                                                 fp64=run_serving(lsg, W, world, precision=lsg.FP64))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -1,8 +1,10 @@
 // serve.cu -- continuous batching of solve requests on one GPU.
 //
 // Requests wait in a queue until a worker slot is free and their device
-// footprint (lsg_footprint_bytes) fits the remaining HBM budget; the first
-// queued request that fits is admitted.  Each admitted request runs on its own
+// footprint (lsg_footprint_bytes) fits the remaining HBM budget; among the
+// queued requests that fit, the one with the smallest footprint is admitted
+// (the earliest on ties), so short solves are not held behind large ones.
+// Each admitted request runs on its own
 // stream -- setup (tables, M, ILU(0)), load vector, PCG -- so the kernels of
 // all in-flight requests overlap on the device, and a finished request frees
 // its slot and budget for the next one at once.  Latency runs from submit to
@@ -86,9 +88,11 @@ static void worker(lsg_server *S)
             std::unique_lock<std::mutex> lk(S->mu);
             for (;;) {
                 if (S->stop) return;
-                auto it = S->queue.begin();
-                for (; it != S->queue.end(); ++it)
-                    if (S->used + it->fp <= S->budget) break;
+                // smallest footprint first among the queued requests that fit (ties:
+                // the earliest), so short solves are not held behind large ones
+                auto it = S->queue.end();
+                for (auto jt = S->queue.begin(); jt != S->queue.end(); ++jt)
+                    if (S->used + jt->fp <= S->budget && (it == S->queue.end() || jt->fp < it->fp)) it = jt;
                 if (it != S->queue.end()) {
                     p = std::move(*it);
                     S->queue.erase(it);
