@@ -68,3 +68,19 @@ def test_fp32_ilu_factors_track_fp64_oracle(lsg):
     zr = O.ilu_solve(ref["LU"], r)
     assert np.linalg.norm(z - zr) / np.linalg.norm(zr) < 1e-4
     ctx.close()
+
+
+@pytest.mark.parametrize("case", [(2, 33, 5), (3, 10, 2)])
+def test_mixed_context_preconditioner_solve(lsg, case):
+    """A mixed context's FP32 ILU(0) factors swept with FP64 vectors (lsg_apply_Minv) against
+    the oracle's FP64 factors and solve: the factors carry FP32 rounding, so the result agrees
+    to a few FP32 ulps relative to the solution, not to FP64 precision."""
+    d, N, T = case
+    p = W.random_exp_problem(d, N, T, 31, 32, 33)
+    ctx = lsg.Context(d, N, T, cuda(p["a"]), cuda(p["b"]), precision=lsg.MIXED_TF32)
+    ref = O.setup(d, N, p["Q"], T, p["a"], p["b"])
+    r = np.random.default_rng(8).standard_normal((N - 1) ** d)
+    z = ctx.apply_Minv(cuda(r)).cpu().numpy()
+    z_ref = O.ilu_solve(ref["LU"], r)
+    assert np.linalg.norm(z - z_ref) / np.linalg.norm(z_ref) < 1e-4
+    ctx.close()
