@@ -478,9 +478,26 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
                 const int i = DIR > 0 ? q : n1 - 1 - q;
                 const V *row = myring + (size_t)(q % SW_D) * RL + (DIR > 0 ? 0 : 1);
                 AT acc0 = lane == 0 ? -srhs[b * n1 + i] : AT(0);
-                if (regpath) {
-                    // a warp-uniform trip count: an FP64 instruction costs its full issue
-                    // time even when every lane is predicated off
+                if (regpath && nk <= 8) {
+                    // up to 8 slots per lane (T <= 9 in 2D): every load is issued (predicated)
+                    // before the first multiply-add; the multiply-adds stop at a warp-uniform
+                    // trip count, since an FP64 instruction costs its full issue time even when
+                    // every lane is predicated off
+                    V fv[8];
+                    AT yv[8];
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) {
+                        const int t0 = lane + 32 * kk;
+                        const bool use = kk < nk && t0 < nslot && !(freshmask >> kk & 1u);
+                        fv[kk] = use ? row[t0] : V(0);
+                        yv[kk] = use ? sy[off[kk] + i] : AT(0);
+                    }
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) {
+                        if (kk >= nk) break;
+                        acc0 += (AT)fv[kk] * yv[kk];
+                    }
+                } else if (regpath) {
 #pragma unroll
                     for (int kk = 0; kk < SW_KS; ++kk) {
                         if (kk >= nk) break;
