@@ -52,7 +52,8 @@ struct SweepArgs {
     unsigned *counter;   // band claim counter
     const int *done;
     int *err;
-    int B;               // lines per CTA
+    int B;               // lines per CTA (k_sweep)
+    int K;               // fresh window (k_sweep_line)
 };
 
 // ---- asynchronous copy and mbarrier primitives (inline PTX, sm_90+) --------
@@ -96,6 +97,11 @@ __device__ __forceinline__ void tma_load(void *sdst, const void *gsrc, unsigned 
         : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Bulk prefetch of global memory into L2 (no completion to wait for).
+__device__ __forceinline__ void prefetch_l2(const void *gsrc, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gsrc), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void named_barrier(int id, int threads)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
@@ -602,6 +608,619 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
     }
 }
 
+// ============================================================================
+// Line-parallel sweep (1D and 2D): one line per CTA, a position's work split
+// over warps.
+//
+// In k_sweep the warp of a line computes each row's whole dot product between
+// two of its positions, so a position costs a full FP64 reduction (~1 us) and a
+// 2D sweep, a chain of about n1 (w+1) + n1 positions, keeps only ~n1/(w+1) lines
+// busy at a time.  Here a CTA owns one line:
+//   * L1_NS stale warps compute T_q = r_q - (every term of row q except the K
+//     newest values of the own line and the K newest of the previous line),
+//     position q by warp q % L1_NS, K positions ahead of the finisher;
+//   * the finisher holds the window of the next K positions in its lanes
+//     (lane j: position s+j) and applies each new value -- y_{s-1} of the own
+//     line, y'_{s+w} of the previous one -- to the whole window with one
+//     multiply-add, so finishing a position is one addition (T_s), two
+//     multiply-adds and, backward, the multiply by the stored 1 / U(i,i);
+//   * a TMA producer streams the line's factor rows into a ring of D rows;
+//   * two loader warps stage the w lines before this one into shared memory
+//     straight from the output vector, and a publisher warp stores the line's
+//     finished values there.  The output is filled with a signalling NaN before
+//     the sweep and every value is stored once, so a word that differs from the
+//     fill is final: no progress words, no fences.
+//     (Arithmetic never produces a signalling NaN.)
+// Lines are claimed in sweep order, so a CTA only waits for lines claimed
+// earlier by running CTAs; every wait is bounded and reports LSG_ERR_TIMEOUT.
+constexpr int L1_NS = 6;                 // stale warps
+constexpr int L1_DT = 32;                // ring of stale results (positions)
+constexpr int L1_WARPS = L1_NS + 5;      // + finisher, TMA producer, two loaders, publisher
+constexpr int L1_D = 32;                 // factor ring depth (rows); rows D further ahead are prefetched to L2
+constexpr int L1_CH = 4;                 // rows per ring barrier (the finisher checks one per L1_CH positions)
+constexpr int L1_KMAX = 8;               // largest fresh window
+
+template <typename AT>
+struct Fill;
+template <>
+struct Fill<double> {
+    using bits = unsigned long long;
+    static constexpr bits v = 0x7FF4A5A5A5A5A5A5ull;
+    __device__ static double val(bits b) { return __longlong_as_double((long long)b); }
+};
+template <>
+struct Fill<float> {
+    using bits = unsigned;
+    static constexpr bits v = 0x7FA5A5A5u;
+    __device__ static float val(bits b) { return __uint_as_float(b); }
+};
+__device__ __forceinline__ unsigned long long ld_poll(const double *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_poll(const float *p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_final(double *p, double v)
+{
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(__double_as_longlong(v)) : "memory");
+}
+__device__ __forceinline__ void st_final(float *p, float v)
+{
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(__float_as_uint(v)) : "memory");
+}
+
+// Fills the output of one sweep with the signalling NaN and resets its line counter.
+template <typename AT>
+__global__ void k_line_fill(AT *out, long long n, unsigned *counter, const int *done)
+{
+    if (done && *done) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0u;
+    typename Fill<AT>::bits *o = reinterpret_cast<typename Fill<AT>::bits *>(out);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        o[e] = Fill<AT>::v;
+}
+
+struct LineSmem {
+    size_t sy, srhs, sT, ring, mbar, meta, total;
+    int RS, PADL, rows;  // row stride, left padding (elements), value rows (halo + own line)
+};
+
+__host__ __device__ inline LineSmem line_layout(int d, int n1, int w, int D, int RL, int vsize, int nslot, int asize)
+{
+    LineSmem L;
+    L.PADL = (w + 1) / 2 * 2;                 // positions -w .. -1 (even: 16-byte row starts)
+    L.RS = (L.PADL + n1 + w + 1) / 2 * 2;     // ... n1 .. n1+w-1 on the right
+    L.rows = d >= 2 ? w + 1 : 1;
+    size_t o = 0;
+    L.sy = o;   o += (size_t)L.rows * L.RS * asize;
+    L.srhs = o; o += (size_t)n1 * asize;
+    o = (o + 15) / 16 * 16;
+    L.sT = o;   o += (size_t)L1_DT * asize;
+    o = (o + 127) / 128 * 128;
+    L.ring = o; o += (size_t)D * RL * vsize;
+    o = (o + 7) / 8 * 8;
+    L.mbar = o; o += (size_t)D * 8;
+    L.meta = o; o += (size_t)nslot * 4;
+    L.total = o;
+    return L;
+}
+
+// Bounded spin until a shared counter reaches `need`; every lane polls with
+// acquire loads and the result is warp-uniform.
+__device__ __forceinline__ bool wait_ge(const volatile int *c, int need, const volatile int *abort_flag, int *err)
+{
+    bool good = true;
+    if (ld_acquire_cta(c) < need) {
+        const long long t0 = clock64();
+        for (int it = 0;; ++it) {
+            if (ld_acquire_cta(c) >= need) break;
+            if (it >= 256) __nanosleep(16);
+            if ((it & 15) == 15) {
+                if (*abort_flag) {
+                    good = false;
+                    break;
+                }
+                if (clock64() - t0 > kSpinBudgetCycles) {
+                    set_err(err, DERR_TIMEOUT);
+                    good = false;
+                    break;
+                }
+            }
+        }
+    }
+    return __all_sync(0xffffffffu, good);
+}
+
+// Bounded poll of a shared word that one writer stores once over the fill
+// pattern: the value itself is the flag (all lanes read the same address; the
+// result is warp-uniform).
+template <typename AT>
+__device__ __forceinline__ bool poll_value(const AT *p, AT &val, const volatile int *abort_flag, int *err)
+{
+    using bits_t = typename Fill<AT>::bits;
+    const volatile bits_t *vp = reinterpret_cast<const volatile bits_t *>(p);
+    bits_t b = *vp;
+    bool good = true;
+    if (b == Fill<AT>::v) {
+        const long long t0 = clock64();
+        for (int it = 0;; ++it) {
+            b = *vp;
+            if (b != Fill<AT>::v) break;
+            if (it >= 256) __nanosleep(16);
+            if ((it & 15) == 15) {
+                if (*abort_flag) {
+                    good = false;
+                    break;
+                }
+                if (clock64() - t0 > kSpinBudgetCycles) {
+                    set_err(err, DERR_TIMEOUT);
+                    good = false;
+                    break;
+                }
+            }
+        }
+    }
+    val = Fill<AT>::val(b);
+    return __all_sync(0xffffffffu, good);
+}
+
+// Bounded wait for an mbarrier phase that also gives up when the CTA aborts.
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t *bar, unsigned parity, const volatile int *abort_flag, int *err)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (int it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 15) == 15) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > kSpinBudgetCycles) {
+                set_err(err, DERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+template <typename V, typename AT, int DIR, int D>
+__global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_constant__ SweepArgs A)
+{
+    if (A.done && *A.done) return;
+    using FB = Fill<AT>;
+    using bits_t = typename FB::bits;
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int NB = D / L1_CH;  // ring barriers, one per chunk of L1_CH rows
+    static_assert(D % L1_CH == 0, "ring depth must be a multiple of the chunk");
+    static_assert(L1_NS == 6, "stale warps sit on sub-partitions 1-3, two each");
+    const StencilGeo G = A.G;
+    const int n1 = G.n1, w = G.w, RL = A.RL, nslot = G.Sc, K = A.K;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const LineSmem Lo = line_layout(G.d, n1, w, D, RL, (int)sizeof(V), nslot, (int)sizeof(AT));
+    const int RS = Lo.RS, PADL = Lo.PADL, own = Lo.rows - 1;  // value row of the own line; row own-h: line v-h
+    AT *sy = (AT *)(smem + Lo.sy);
+    AT *srhs = (AT *)(smem + Lo.srhs);
+    AT *sT = (AT *)(smem + Lo.sT);
+    V *ring = (V *)(smem + Lo.ring);
+    uint64_t *mbar = (uint64_t *)(smem + Lo.mbar);
+    unsigned *meta = (unsigned *)(smem + Lo.meta);
+    __shared__ volatile int s_abort;
+    __shared__ volatile int s_prog;            // positions the finisher completed
+    __shared__ volatile int s_near, s_near2;   // positions of lines v-1 and v-2 staged in shared memory
+    __shared__ volatile int s_far;             // ... of lines v-3 .. v-w (minimum)
+    __shared__ int s_fown[32], s_fprev[32];    // slots of the window's fresh terms (lane j)
+    __shared__ unsigned s_mask[L1_KMAX][32];   // stale warps: window slots per lane (see below)
+    __shared__ long long s_line;
+    __shared__ int s_issued;                   // chunks the producer issued (this line)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // warp roles: the finisher alone on sub-partition 0 with the producer (no FP64
+    // work), the stale warps two per sub-partition 1-3, the loaders and the publisher
+    enum { R_FIN, R_STALE, R_PROD, R_NEAR, R_FAR, R_PUB };
+    const int role = wid == 0 ? R_FIN : wid == 4 ? R_PROD : wid == 8 ? R_NEAR : wid == 9 ? R_FAR : wid == 10 ? R_PUB
+                                                                                                            : R_STALE;
+    const int sw = wid < 4 ? wid - 1 : wid - 2;  // stale warp index (R_STALE)
+    const AT *rhs = (const AT *)A.rhs;
+    AT *out = (AT *)A.out;
+    const V *F = (const V *)A.F;
+
+    if (threadIdx.x < 32) s_fown[threadIdx.x] = -1, s_fprev[threadIdx.x] = -1;
+    __syncthreads();
+    for (int t = threadIdx.x; t < nslot; t += blockDim.x) {
+        const int s = DIR > 0 ? t : G.Sc + 1 + t;
+        int dx, dy, dz;
+        slot_offsets(G, s, dx, dy, dz);
+        meta[t] = (unsigned)(dx + 128) | ((unsigned)(dy + 128) << 8) | ((unsigned)(dz + 128) << 16);
+        // in sweep order: own-line position q-m is offset dx = -DIR m; previous-line
+        // position q+w-j is offset (DIR (w-j), -DIR)
+        const int m = -DIR * dx, jj = w - DIR * dx;
+        if (dy == 0 && dz == 0 && m >= 1 && m <= K) s_fown[m - 1] = t;
+        if (G.d >= 2 && dz == 0 && dy == -DIR && jj >= 0 && jj < K) s_fprev[jj] = t;
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NB; ++i) mbar_init(&mbar[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // chunk c (rows L1_CH c ..) lands in ring rows (L1_CH c) % D .. and completes
+    // barrier c % NB; per line that barrier takes ceil((nch - b) / NB) chunks, so
+    // the phase parity of row q in this CTA's line `it` is:
+    const int nch = (n1 + L1_CH - 1) / L1_CH;
+    auto parity = [&](int it, int q) -> unsigned {
+        const int c = q / L1_CH, cnt = (nch - c % NB + NB - 1) / NB;
+        return (unsigned)(((it & cnt) ^ (c / NB)) & 1);
+    };
+    auto wait_chunk = [&](int it, int q) -> bool {
+        return __all_sync(FULL, mbar_wait_ab(&mbar[(q / L1_CH) % NB], parity(it, q), &s_abort, A.err));
+    };
+
+    // stale warps: the window's slots among a lane's (bit kk: slot lane + 32 kk);
+    // s_mask[l] takes the previous-line slots jj <= l only (the first positions of
+    // a line), s_mask[K-1] all of them
+    const int nk = (nslot + 31) / 32;
+    for (int e = threadIdx.x; e < L1_KMAX * 32; e += blockDim.x) {
+        const int l = e / 32, ln = e % 32;
+        unsigned mk = 0;
+        for (int kk = 0; kk < SW_KS && kk < nk; ++kk) {
+            const int t = ln + 32 * kk;
+            for (int f = 0; f < K; ++f)
+                if (t == s_fown[f] || (f <= l && t == s_fprev[f])) mk |= 1u << kk;
+        }
+        s_mask[l][ln] = mk;
+    }
+    __syncthreads();
+    int off[SW_KS];
+    unsigned freshmask = 0;
+    if (role == R_STALE) {
+#pragma unroll
+        for (int kk = 0; kk < SW_KS; ++kk) {
+            const int t = lane + 32 * kk;
+            off[kk] = 0;
+            if (t < nslot) {
+                const unsigned m = meta[t];
+                const int dx = (int)(m & 255u) - 128, dy = (int)((m >> 8) & 255u) - 128;
+                off[kk] = (own + DIR * dy) * RS + PADL + dx;
+            }
+        }
+        freshmask = s_mask[K - 1][lane];
+    }
+
+    for (int it = 0;; ++it) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_line = atomicAdd(A.counter, 1u);
+            s_prog = 0;
+            s_near = 0;
+            s_near2 = 0;
+            s_far = 0;
+            s_issued = 0;
+            s_abort = (*(volatile int *)A.err != 0) ? 1 : 0;
+        }
+        __syncthreads();
+        const long long v = s_line;
+        if (v >= G.nlines || s_abort) return;  // no copy is in flight between lines
+        const long long line = DIR > 0 ? v : G.nlines - 1 - v;
+        // the finisher polls the values of line v-1 and the stale results for the
+        // fill pattern; everything else starts at zero (padding, absent lines)
+        const bool prev_exists = G.d >= 2 && v >= 1;
+        bits_t *ybits = reinterpret_cast<bits_t *>(sy);
+        for (int e = threadIdx.x; e < Lo.rows * RS; e += blockDim.x) {
+            const int r = e / RS, c = e - r * RS - PADL;
+            ybits[e] = (prev_exists && r == own - 1 && c >= 0 && c < n1) ? FB::v : bits_t(0);
+        }
+        for (int e = threadIdx.x; e < L1_DT; e += blockDim.x) reinterpret_cast<bits_t *>(sT)[e] = FB::v;
+        for (int q = threadIdx.x; q < n1; q += blockDim.x) srhs[q] = rhs[q + (long long)n1 * line];
+        if (threadIdx.x == 0) {
+            // lines before the first one, and lines of 1D problems, do not exist
+            if (G.d < 2 || v < 1) s_near = n1;
+            if (G.d < 2 || v < 2) s_near2 = n1;
+            if (G.d < 2 || v < 3 || w < 3) s_far = n1;
+        }
+        __syncthreads();
+        bool ok = true;
+
+        if (role == R_FIN) {
+            // ---------------------------------------------------------------- finisher
+            const int j = lane;
+            const int fo_t = j < K ? s_fown[j] : -1, fp_t = j < K ? s_fprev[j] : -1;
+            const int myrow = own * RS + PADL;
+            const int prevoff = G.d >= 2 ? (own - 1) * RS + PADL + DIR * w : 0;
+            AT Gw = 0, yb = 0;  // lane j: fresh part of position s+j; y_{s-1}
+            for (int q = 0; q <= K - 2 && q < n1 && ok; q += L1_CH) ok = wait_chunk(it, q);
+            if (ok && K - 1 < n1 && (K - 1) % L1_CH == 0) ok = wait_chunk(it, K - 1);
+            // operands of the next step, loaded at the end of the previous one so that
+            // their latency overlaps the shuffles: the window's factors, the stale part
+            // and the previous line's value (zero past the line's end; both are final
+            // once they differ from the fill)
+            AT fo = 0, fp = 0, ri = 1;
+            auto load_factors = [&](int s) {
+                const int qj = s + j;
+                fo = 0, fp = 0, ri = 1;
+                if (j < K && qj < n1) {
+                    const V *row = ring + (size_t)(qj % D) * RL + (DIR > 0 ? 0 : 1);
+                    if (fo_t >= 0) fo = (AT)row[fo_t];
+                    if (fp_t >= 0) fp = (AT)row[fp_t];
+                    if (DIR < 0) ri = (AT)row[RL - 2];  // 1 / U(i,i), stored by the factorisation
+                }
+            };
+            const volatile bits_t *vT = reinterpret_cast<const volatile bits_t *>(sT);
+            const volatile bits_t *vP = reinterpret_cast<const volatile bits_t *>(sy + prevoff);
+            bits_t tb = 0, pb = 0;
+            if (ok) {
+                load_factors(0);
+                tb = vT[0];
+                pb = G.d >= 2 ? vP[DIR > 0 ? 0 : n1 - 1] : bits_t(0);
+            }
+            for (int s = 0; s < n1 && ok; ++s) {
+                const int i = DIR > 0 ? s : n1 - 1 - s;
+                AT Tv = FB::val(tb), yp = FB::val(pb);
+                if (tb == FB::v) ok = poll_value(&sT[s % L1_DT], Tv, &s_abort, A.err);
+                if (ok && pb == FB::v) ok = poll_value(&sy[prevoff + i], yp, &s_abort, A.err);
+                if (!ok) break;
+                __syncwarp();
+                if (lane == 0) *reinterpret_cast<volatile bits_t *>(&sT[s % L1_DT]) = FB::v;
+                Gw += (j == 0) ? Tv : AT(0);
+                Gw = fma(-fp, yp, Gw);
+                // the own line's newest value last: the only step on the loop-carried chain
+                Gw = fma(-fo, yb, Gw);
+                const AT val = DIR < 0 ? Gw * ri : Gw;
+                if (lane == 0) {
+                    sy[myrow + i] = val;
+                    st_release_cta(&s_prog, s + 1);
+                }
+                if (s + 1 < n1) {
+                    const int qn = s + K;  // the row entering the window next
+                    if (qn < n1 && qn % L1_CH == 0) {
+                        ok = wait_chunk(it, qn);
+                        if (!ok) break;
+                    }
+                    load_factors(s + 1);
+                    tb = vT[(s + 1) % L1_DT];
+                    pb = G.d >= 2 ? vP[DIR > 0 ? s + 1 : n1 - 2 - s] : bits_t(0);
+                }
+                yb = __shfl_sync(FULL, val, 0);
+                Gw = __shfl_down_sync(FULL, Gw, 1);
+                if (j >= K - 1) Gw = AT(0);
+            }
+        } else if (role == R_STALE) {
+            // ---------------------------------------------------------------- stale warps
+            // T_q = r_q - S_q, S_q every term of row q but the window's: own-line
+            // positions < q-K and previous-line positions < max(w, q+w-K+1) are final
+            // once the finisher has done q-K positions and line v-1 is staged that far
+            for (int q = sw; q < n1 && ok; q += L1_NS) {
+                ok = wait_ge(&s_prog, q - K, &s_abort, A.err) &&
+                     wait_ge(&s_near, min(max(w, q + w - K + 1), n1), &s_abort, A.err) &&
+                     wait_ge(&s_near2, min(q + w + 1, n1), &s_abort, A.err) &&
+                     wait_ge(&s_far, min(q + w + 1, n1), &s_abort, A.err) && wait_chunk(it, q);
+                if (!ok) break;
+                const int i = DIR > 0 ? q : n1 - 1 - q;
+                const V *row = ring + (size_t)(q % D) * RL + (DIR > 0 ? 0 : 1);
+                // the finisher's first step is 0, so the window of position q < K-1 only
+                // receives previous-line values from position w on: the older ones
+                // (slots jj > q) stay in the stale part
+                const unsigned fm = q >= K - 1 ? freshmask : s_mask[q][lane];
+                AT acc0 = lane == 0 ? -srhs[i] : AT(0);
+                if (nk <= 8) {
+                    // every load is issued before the first multiply-add; the
+                    // multiply-adds stop at a warp-uniform trip count
+                    V fv[8];
+                    AT yv[8];
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) {
+                        const int t0 = lane + 32 * kk;
+                        const bool use = kk < nk && t0 < nslot && !(fm >> kk & 1u);
+                        fv[kk] = use ? row[t0] : V(0);
+                        yv[kk] = use ? sy[off[kk] + i] : AT(0);
+                    }
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) {
+                        if (kk >= nk) break;
+                        acc0 += (AT)fv[kk] * yv[kk];
+                    }
+                } else {
+#pragma unroll
+                    for (int kk = 0; kk < SW_KS; ++kk) {
+                        if (kk >= nk) break;
+                        const int t0 = lane + 32 * kk;
+                        if (t0 < nslot && !(fm >> kk & 1u)) acc0 += (AT)row[t0] * sy[off[kk] + i];
+                    }
+                }
+                const AT T = -warp_sum(acc0);
+                if (lane == 0) *reinterpret_cast<volatile AT *>(&sT[q % L1_DT]) = T;
+            }
+        } else if (role == R_PROD) {
+            // ---------------------------------------------------------------- TMA producer
+            // chunk c goes to its ring rows once the finisher has done the chunk that
+            // held them (c - NB; the stale warps are done with it by then too); rows
+            // up to 2D ahead are prefetched to L2, so a ring copy rarely waits for HBM
+            if (lane == 0) {
+                const unsigned rowbytes = (unsigned)(RL * sizeof(V));
+                auto grow = [&](int q) { return F + ((DIR > 0 ? q : n1 - 1 - q) + (long long)n1 * line) * RL; };
+                for (int pq = D; pq < 2 * D && pq < n1; ++pq) prefetch_l2(grow(pq), rowbytes);
+                int c = 0;
+                const long long t0 = clock64();
+                for (int itp = 0; c < nch; ++itp) {
+                    if (s_abort) break;
+                    const int fin = s_prog;
+                    __threadfence_block();
+                    bool any = false;
+                    while (c < nch && L1_CH * c - D + L1_CH <= fin) {
+                        if (!any) fence_proxy_async();
+                        any = true;
+                        const int q0 = L1_CH * c, q1 = min(q0 + L1_CH, n1);
+                        uint64_t *bar = &mbar[c % NB];
+                        mbar_expect_tx(bar, (unsigned)(q1 - q0) * rowbytes);
+                        for (int q = q0; q < q1; ++q) {
+                            tma_load(ring + (size_t)(q % D) * RL, grow(q), rowbytes, bar);
+                            if (q + 2 * D < n1) prefetch_l2(grow(q + 2 * D), rowbytes);
+                        }
+                        ++c;
+                    }
+                    if (!any) {
+                        if (itp > 64) __nanosleep(32);
+                        if (clock64() - t0 > 4 * kSpinBudgetCycles) {
+                            set_err(A.err, DERR_TIMEOUT);
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+                s_issued = c;
+            }
+        } else if (role == R_NEAR) {
+            // ---------------------------------------------------------------- loader: lines v-1, v-2
+            // 32 positions of each line per poll; the staged prefix is what differs from the fill
+            int b1 = s_near, b2 = s_near2;
+            const long long l1 = DIR > 0 ? v - 1 : G.nlines - v;
+            const long long l2 = DIR > 0 ? v - 2 : G.nlines + 1 - v;
+            AT *r1 = sy + (own - 1) * RS + PADL, *r2 = sy + (own - 2) * RS + PADL;
+            const long long t0 = clock64();
+            for (int itp = 0; b1 < n1 || b2 < n1; ++itp) {
+                const int p1 = b1 + lane, p2 = b2 + lane;
+                const int i1 = DIR > 0 ? p1 : n1 - 1 - p1, i2 = DIR > 0 ? p2 : n1 - 1 - p2;
+                bits_t x1 = FB::v, x2 = FB::v;
+                if (p1 < n1) x1 = ld_poll(out + l1 * n1 + i1);
+                if (p2 < n1) x2 = ld_poll(out + l2 * n1 + i2);
+                const unsigned m1 = __ballot_sync(FULL, p1 < n1 && x1 != FB::v);
+                const unsigned m2 = __ballot_sync(FULL, p2 < n1 && x2 != FB::v);
+                const int c1 = m1 == FULL ? 32 : __ffs(~m1) - 1;
+                const int c2 = m2 == FULL ? 32 : __ffs(~m2) - 1;
+                if (lane < c1) r1[i1] = FB::val(x1);
+                if (lane < c2) r2[i2] = FB::val(x2);
+                if (c1 + c2 > 0) {
+                    __syncwarp();
+                    if (lane == 0) {
+                        __threadfence_block();
+                        if (c2) st_release_cta(&s_near2, b2 + c2);
+                        if (c1) st_release_cta(&s_near, b1 + c1);
+                    }
+                    b1 += c1;
+                    b2 += c2;
+                } else {
+                    if (itp > 64) __nanosleep(32);
+                    if ((itp & 15) == 15) {
+                        bool stop = s_abort != 0 || *(volatile int *)A.err != 0;
+                        if (clock64() - t0 > 4 * kSpinBudgetCycles) {
+                            if (lane == 0) set_err(A.err, DERR_TIMEOUT);
+                            stop = true;
+                        }
+                        if (__any_sync(FULL, stop)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+            }
+        } else if (role == R_PUB) {
+            // ---------------------------------------------------------------- publisher
+            // stores finished values to the output (the finisher touches shared memory
+            // only, so no fence of its waits on a global store)
+            const AT *yrow = sy + own * RS + PADL;
+            AT *oline = out + (long long)n1 * line;
+            int pub = 0;
+            const long long t0 = clock64();
+            for (int itp = 0; pub < n1; ++itp) {
+                const int fin = ld_acquire_cta(&s_prog);
+                if (fin > pub) {
+                    for (int p = pub + lane; p < fin; p += 32) {
+                        const int i = DIR > 0 ? p : n1 - 1 - p;
+                        st_final(oline + i, yrow[i]);
+                    }
+                    pub = fin;
+                } else {
+                    if (itp > 64) __nanosleep(16);
+                    if ((itp & 15) == 15) {
+                        bool stop = s_abort != 0;
+                        if (clock64() - t0 > 4 * kSpinBudgetCycles) {
+                            if (lane == 0) set_err(A.err, DERR_TIMEOUT);
+                            stop = true;
+                        }
+                        if (__any_sync(FULL, stop)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+            }
+        } else if (role == R_FAR) {
+            // ---------------------------------------------------------------- loader: lines v-3 .. v-w
+            // lane h holds how far line v-h is staged
+            int my = (G.d >= 2 && lane >= 3 && lane <= w && v - lane >= 0) ? 0 : n1;
+            const long long t0 = clock64();
+            for (int itp = 0;; ++itp) {
+                if ((int)__reduce_min_sync(FULL, (unsigned)my) >= n1) break;
+                bool moved = false;
+                for (int h0 = 3; h0 <= w; h0 += 8) {
+                    bits_t x[8];
+                    int st[8], ii[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int h = h0 + u;
+                        st[u] = __shfl_sync(FULL, my, h & 31);
+                        if (h > w) st[u] = n1;
+                        const int p = st[u] + lane;
+                        ii[u] = DIR > 0 ? p : n1 - 1 - p;
+                        x[u] = FB::v;
+                        if (p < n1) {
+                            const long long hl = DIR > 0 ? v - h : G.nlines - 1 - (v - h);
+                            x[u] = ld_poll(out + hl * n1 + ii[u]);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int h = h0 + u;
+                        const int p = st[u] + lane;
+                        const unsigned m = __ballot_sync(FULL, p < n1 && x[u] != FB::v);
+                        const int c = m == FULL ? 32 : __ffs(~m) - 1;
+                        if (c > 0) {
+                            if (lane < c) sy[(own - h) * RS + PADL + ii[u]] = FB::val(x[u]);
+                            moved = true;
+                            if (lane == h) my = st[u] + c;
+                        }
+                    }
+                }
+                if (moved) {
+                    __syncwarp();
+                    const int far = (int)__reduce_min_sync(FULL, (unsigned)my);
+                    if (lane == 0) {
+                        __threadfence_block();
+                        st_release_cta(&s_far, far);
+                    }
+                } else {
+                    if (itp > 64) __nanosleep(32);
+                    if ((itp & 15) == 15) {
+                        bool stop = s_abort != 0 || *(volatile int *)A.err != 0;
+                        if (clock64() - t0 > 4 * kSpinBudgetCycles) {
+                            if (lane == 0) set_err(A.err, DERR_TIMEOUT);
+                            stop = true;
+                        }
+                        if (__any_sync(FULL, stop)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+            }
+        }
+        if (!ok && lane == 0) s_abort = 1;
+        __syncthreads();
+        if (s_abort) {
+            // the last chunk issued on each ring barrier must land before the CTA exits
+            if (threadIdx.x == 0) {
+                const int iss = s_issued;
+                for (int b = 0; b < NB && b < iss; ++b) {
+                    const int cl = b + ((iss - 1 - b) / NB) * NB;
+                    mbar_wait(&mbar[b], parity(it, cl * L1_CH), A.err);
+                }
+            }
+            return;
+        }
+    }
+}
+
 template <typename V, typename AT, int DIR, int D>
 static int launch_sweep(const SweepArgs &A, size_t smem, unsigned grid, cudaStream_t s)
 {
@@ -623,18 +1242,91 @@ static int launch_sweep_d(const SweepArgs &A, int D, size_t smem, unsigned grid,
     return launch_sweep<V, AT, DIR, 4>(A, smem, grid, s);
 }
 
+template <typename V, typename AT, int DIR>
+static int launch_line(const SweepArgs &A, size_t smem, unsigned grid, cudaStream_t s)
+{
+    static size_t attr = 0;  // benign race: setting the attribute twice is harmless
+    if (smem > attr) {
+        LSG_CK(cudaFuncSetAttribute(k_sweep_line<V, AT, DIR, L1_D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+        attr = smem;
+    }
+    ::lsg::count_launch();
+    k_sweep_line<V, AT, DIR, L1_D><<<grid, 32 * L1_WARPS, smem, s>>>(A);
+    LSG_CK(cudaGetLastError());
+    return LSG_OK;
+}
+
+template <typename AT>
+static int launch_fill(AT *out, long long n, unsigned *counter, const int *done, int nsm, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 4LL * nsm));
+    ::lsg::count_launch();
+    k_line_fill<AT><<<grid, 256, 0, s>>>(out, n, counter, done);
+    LSG_CK(cudaGetLastError());
+    return LSG_OK;
+}
+
+// Both sweeps with the line-parallel kernel (1D and 2D).
+template <typename V, typename AT>
+static int sweeps_line(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done, cudaStream_t s, size_t smf,
+                       size_t smb)
+{
+    const Geom &g = c->g;
+    SweepArgs A{};
+    A.G = sgeo(g);
+    A.done = done;
+    A.err = c->err;
+    A.B = 1;
+    // fresh window: the stale part of a row may start K positions before the row
+    // is finished, which covers its ~1 us FP64 reduction at a few hundred ns per position
+    A.K = 8;
+    int dev = 0, nsm = 0;
+    LSG_CK(cudaGetDevice(&dev));
+    LSG_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned grid = (unsigned)std::min<long long>(g.nlines, nsm);
+    int slot;
+    // forward: L y = r
+    A.F = c->Lv;
+    A.RL = g.SL;
+    A.rhs = r;
+    A.out = ytmp;
+    A.counter = c->counters + 1;
+    LSG_TRY(prof_begin(c, PROF_SWEEP_L, s, &slot));
+    LSG_TRY(launch_fill<AT>(ytmp, g.n, c->counters + 1, done, nsm, s));
+    LSG_TRY((launch_line<V, AT, 1>(A, smf, grid, s)));
+    LSG_TRY(prof_end(c, slot, s));
+    // backward: U z = y (z is filled only now: it may be the same vector as r)
+    A.F = c->Uv;
+    A.RL = g.SU;
+    A.rhs = ytmp;
+    A.out = z;
+    A.counter = c->counters + 2;
+    LSG_TRY(prof_begin(c, PROF_SWEEP_U, s, &slot));
+    LSG_TRY(launch_fill<AT>(z, g.n, c->counters + 2, done, nsm, s));
+    LSG_TRY((launch_line<V, AT, -1>(A, smb, grid, s)));
+    LSG_TRY(prof_end(c, slot, s));
+    return LSG_OK;
+}
+
 template <typename V, typename AT>
 static int sweeps(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done, cudaStream_t s)
 {
     const Geom &g = c->g;
-    SweepArgs A;
+    const size_t budget = 210 * 1024;
+    if (g.d <= 2 && g.Sc <= 32 * SW_KS && g.w <= 31) {
+        const int vs = (int)sizeof(V), as = (int)sizeof(AT);
+        const size_t smf = line_layout(g.d, g.n1, g.w, L1_D, g.SL, vs, g.Sc, as).total;
+        const size_t smb = line_layout(g.d, g.n1, g.w, L1_D, g.SU, vs, g.Sc, as).total;
+        if (std::max(smf, smb) <= budget) return sweeps_line<V, AT>(c, r, z, ytmp, done, s, smf, smb);
+    }
+    SweepArgs A{};
     A.G = sgeo(g);
     A.done = done;
     A.err = c->err;
     // lines per CTA: one per SM sub-partition (an FP64 warp instruction occupies its
     // sub-partition's FP64 unit for ~64 clocks; in FP32 a second line per
     // sub-partition measured slower too); fewer if shared memory runs out
-    const size_t budget = 210 * 1024;
     const int RLmax = std::max(g.SL, g.SU);
     const int vs = (int)sizeof(V), as = (int)sizeof(AT);
     int B = 4;
