@@ -675,6 +675,42 @@ __device__ __forceinline__ void st_final(float *p, float v)
     asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(__float_as_uint(v)) : "memory");
 }
 
+// Shared-memory accesses by 32-bit shared address (the finisher's hot loop).
+__device__ __forceinline__ unsigned long long lds_vol(unsigned a, unsigned long long)
+{
+    unsigned long long v;
+    asm volatile("ld.volatile.shared.b64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned lds_vol(unsigned a, unsigned)
+{
+    unsigned v;
+    asm volatile("ld.volatile.shared.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts_vol(unsigned a, unsigned long long v)
+{
+    asm volatile("st.volatile.shared.b64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+__device__ __forceinline__ void sts_vol(unsigned a, unsigned v)
+{
+    asm volatile("st.volatile.shared.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ double lds_val(unsigned a, double)
+{
+    double v;
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float lds_val(unsigned a, float)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts_val(unsigned a, double v) { asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory"); }
+__device__ __forceinline__ void sts_val(unsigned a, float v) { asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory"); }
+
 // Fills the output of one sweep with the signalling NaN and resets its line counter.
 template <typename AT>
 __global__ void k_line_fill(AT *out, long long n, unsigned *counter, const int *done)
@@ -813,7 +849,6 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
     __shared__ volatile int s_near, s_near2;   // positions of lines v-1 and v-2 staged in shared memory
     __shared__ volatile int s_far;             // ... of lines v-3 .. v-w (minimum)
     __shared__ int s_fown[32], s_fprev[32];    // slots of the window's fresh terms (lane j)
-    __shared__ unsigned s_mask[L1_KMAX][32];   // stale warps: window slots per lane (see below)
     __shared__ long long s_line;
     __shared__ int s_issued;                   // chunks the producer issued (this line)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -857,21 +892,9 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
         return __all_sync(FULL, mbar_wait_ab(&mbar[(q / L1_CH) % NB], parity(it, q), &s_abort, A.err));
     };
 
-    // stale warps: the window's slots among a lane's (bit kk: slot lane + 32 kk);
-    // s_mask[l] takes the previous-line slots jj <= l only (the first positions of
-    // a line), s_mask[K-1] all of them
+    // stale warps: register-resident stencil offsets (row buffers of this CTA) and
+    // the window's slots among this lane's (bit kk: slot lane + 32 kk)
     const int nk = (nslot + 31) / 32;
-    for (int e = threadIdx.x; e < L1_KMAX * 32; e += blockDim.x) {
-        const int l = e / 32, ln = e % 32;
-        unsigned mk = 0;
-        for (int kk = 0; kk < SW_KS && kk < nk; ++kk) {
-            const int t = ln + 32 * kk;
-            for (int f = 0; f < K; ++f)
-                if (t == s_fown[f] || (f <= l && t == s_fprev[f])) mk |= 1u << kk;
-        }
-        s_mask[l][ln] = mk;
-    }
-    __syncthreads();
     int off[SW_KS];
     unsigned freshmask = 0;
     if (role == R_STALE) {
@@ -885,7 +908,11 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
                 off[kk] = (own + DIR * dy) * RS + PADL + dx;
             }
         }
-        freshmask = s_mask[K - 1][lane];
+        for (int kk = 0; kk < SW_KS && kk < nk; ++kk) {
+            const int t = lane + 32 * kk;
+            for (int f = 0; f < K; ++f)
+                if (t == s_fown[f] || t == s_fprev[f]) freshmask |= 1u << kk;
+        }
     }
 
     for (int it = 0;; ++it) {
@@ -928,80 +955,97 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
             const int fo_t = j < K ? s_fown[j] : -1, fp_t = j < K ? s_fprev[j] : -1;
             const int myrow = own * RS + PADL;
             const int prevoff = G.d >= 2 ? (own - 1) * RS + PADL + DIR * w : 0;
-            AT Gw = 0, yb = 0;  // lane j: fresh part of position s+j; y_{s-1}
-            for (int q = 0; q <= K - 2 && q < n1 && ok; q += L1_CH) ok = wait_chunk(it, q);
-            if (ok && K - 1 < n1 && (K - 1) % L1_CH == 0) ok = wait_chunk(it, K - 1);
+            // lane j holds Gw, the fresh part of position s+j so far; yb = y_{s-1}.  The
+            // window starts K-1 steps before position 0 so that every position receives
+            // its K newest previous-line values here (steps s < 0 only apply those).
+            AT Gw = 0, yb = 0;
+            const int s0 = -(K - 1);
+            if (n1 > 0) ok = wait_chunk(it, 0);
             // operands of the next step, loaded at the end of the previous one so that
             // their latency overlaps the shuffles: the window's factors, the stale part
-            // and the previous line's value (zero past the line's end; both are final
+            // and the previous line's value (zero past the line's ends; both are final
             // once they differ from the fill)
             AT fo = 0, fp = 0, ri = 1;
+            // shared addresses: this lane's factor slots in ring row 0, the stale ring,
+            // the previous line's row (at position 0) and the own row
+            const unsigned a_ring = smem_u32(ring) + (unsigned)((DIR > 0 ? 0 : 1) * (int)sizeof(V));
+            const unsigned a_fo = a_ring + (unsigned)(max(fo_t, 0) * (int)sizeof(V));
+            const unsigned a_fp = a_ring + (unsigned)(max(fp_t, 0) * (int)sizeof(V));
+            const unsigned a_ri = a_ring + (unsigned)((RL - 2) * (int)sizeof(V));
+            const unsigned rowb = (unsigned)(RL * (int)sizeof(V));
+            const unsigned a_T = smem_u32(sT), a_P = smem_u32(sy + prevoff), a_Y = smem_u32(sy + myrow);
             auto load_factors = [&](int s) {
                 const int qj = s + j;
-                fo = 0, fp = 0, ri = 1;
-                if (j < K && qj < n1) {
-                    const V *row = ring + (size_t)(qj % D) * RL + (DIR > 0 ? 0 : 1);
-                    if (fo_t >= 0) fo = (AT)row[fo_t];
-                    if (fp_t >= 0) fp = (AT)row[fp_t];
-                    if (DIR < 0) ri = (AT)row[RL - 2];  // 1 / U(i,i), stored by the factorisation
-                }
+                const bool in = j < K && qj >= 0 && qj < n1;
+                const unsigned ro = (unsigned)(qj & (D - 1)) * rowb;
+                fo = (in && fo_t >= 0) ? (AT)lds_val(a_fo + ro, V(0)) : AT(0);
+                fp = (in && fp_t >= 0) ? (AT)lds_val(a_fp + ro, V(0)) : AT(0);
+                if (DIR < 0) ri = in ? (AT)lds_val(a_ri + ro, V(0)) : AT(1);  // 1 / U(i,i), stored by the factorisation
             };
-            const volatile bits_t *vT = reinterpret_cast<const volatile bits_t *>(sT);
-            const volatile bits_t *vP = reinterpret_cast<const volatile bits_t *>(sy + prevoff);
+            auto load_T = [&](int s) -> bits_t {
+                return s >= 0 ? lds_vol(a_T + (unsigned)((s % L1_DT) * (int)sizeof(AT)), bits_t(0)) : bits_t(0);
+            };
+            auto load_P = [&](int s) -> bits_t {
+                return (G.d >= 2 && s + w >= 0)
+                           ? lds_vol(a_P + (unsigned)((DIR > 0 ? s : n1 - 1 - s) * (int)sizeof(AT)), bits_t(0))
+                           : bits_t(0);
+            };
             bits_t tb = 0, pb = 0;
-            if (ok) {
-                load_factors(0);
-                tb = vT[0];
-                pb = G.d >= 2 ? vP[DIR > 0 ? 0 : n1 - 1] : bits_t(0);
+            auto next_operands = [&](int s) -> bool {  // for step s: the entering row's chunk, then loads
+                const int qn = s + K - 1;
+                if (qn > 0 && qn < n1 && qn % L1_CH == 0 && !wait_chunk(it, qn)) return false;
+                load_factors(s);
+                tb = load_T(s);
+                pb = load_P(s);
+                return true;
+            };
+            if (ok) ok = next_operands(s0);
+            // steps before position 0: previous-line values only
+            for (int s = s0; s < 0 && ok; ++s) {
+                AT yp = FB::val(pb);
+                if (pb == FB::v) ok = poll_value(&sy[prevoff + (DIR > 0 ? s : n1 - 1 - s)], yp, &s_abort, A.err);
+                if (!ok) break;
+                const AT r = fma(-fp, yp, Gw);
+                Gw = __shfl_down_sync(FULL, r, 1);
+                if (j >= K - 1) Gw = AT(0);
+                ok = next_operands(s + 1);
             }
             for (int s = 0; s < n1 && ok; ++s) {
                 const int i = DIR > 0 ? s : n1 - 1 - s;
                 AT Tv = FB::val(tb), yp = FB::val(pb);
-                if (tb == FB::v) ok = poll_value(&sT[s % L1_DT], Tv, &s_abort, A.err);
-                if (ok && pb == FB::v) ok = poll_value(&sy[prevoff + i], yp, &s_abort, A.err);
-                if (!ok) break;
-                __syncwarp();
-                if (lane == 0) *reinterpret_cast<volatile bits_t *>(&sT[s % L1_DT]) = FB::v;
-                Gw += (j == 0) ? Tv : AT(0);
-                Gw = fma(-fp, yp, Gw);
-                // the own line's newest value last: the only step on the loop-carried chain
-                Gw = fma(-fo, yb, Gw);
-                const AT val = DIR < 0 ? Gw * ri : Gw;
-                if (lane == 0) {
-                    sy[myrow + i] = val;
-                    st_release_cta(&s_prog, s + 1);
+                if (tb == FB::v || pb == FB::v) {
+                    ok = poll_value(&sT[s % L1_DT], Tv, &s_abort, A.err) &&
+                         (G.d < 2 || poll_value(&sy[prevoff + i], yp, &s_abort, A.err));
+                    if (!ok) break;
                 }
-                if (s + 1 < n1) {
-                    const int qn = s + K;  // the row entering the window next
-                    if (qn < n1 && qn % L1_CH == 0) {
-                        ok = wait_chunk(it, qn);
-                        if (!ok) break;
-                    }
-                    load_factors(s + 1);
-                    tb = vT[(s + 1) % L1_DT];
-                    pb = G.d >= 2 ? vP[DIR > 0 ? s + 1 : n1 - 2 - s] : bits_t(0);
-                }
-                yb = __shfl_sync(FULL, val, 0);
-                Gw = __shfl_down_sync(FULL, Gw, 1);
+                // the stale part and the previous line's value go into a separate
+                // register, off the loop-carried chain (add, multiply-add by y_{s-1})
+                const AT Bv = fma(-fp, yp, (j == 0) ? Tv : AT(0));
+                const AT r = fma(-fo, yb, Gw + Bv);
+                yb = __shfl_sync(FULL, DIR < 0 ? r * ri : r, 0);
+                // every lane has read this step's stale slot (the shuffle synchronises
+                // the warp): refill it, then publish y_s (all lanes store the same value)
+                sts_vol(a_T + (unsigned)((s % L1_DT) * (int)sizeof(AT)), FB::v);
+                sts_val(a_Y + (unsigned)(i * (int)sizeof(AT)), yb);
+                st_release_cta(&s_prog, s + 1);
+                Gw = __shfl_down_sync(FULL, r, 1);
                 if (j >= K - 1) Gw = AT(0);
+                if (s + 1 < n1) ok = next_operands(s + 1);
             }
         } else if (role == R_STALE) {
             // ---------------------------------------------------------------- stale warps
             // T_q = r_q - S_q, S_q every term of row q but the window's: own-line
-            // positions < q-K and previous-line positions < max(w, q+w-K+1) are final
-            // once the finisher has done q-K positions and line v-1 is staged that far
+            // positions < q-K and previous-line positions <= q+w-K are final once the
+            // finisher has done q-K positions and line v-1 is staged that far
             for (int q = sw; q < n1 && ok; q += L1_NS) {
                 ok = wait_ge(&s_prog, q - K, &s_abort, A.err) &&
-                     wait_ge(&s_near, min(max(w, q + w - K + 1), n1), &s_abort, A.err) &&
+                     wait_ge(&s_near, min(max(0, q + w - K + 1), n1), &s_abort, A.err) &&
                      wait_ge(&s_near2, min(q + w + 1, n1), &s_abort, A.err) &&
                      wait_ge(&s_far, min(q + w + 1, n1), &s_abort, A.err) && wait_chunk(it, q);
                 if (!ok) break;
                 const int i = DIR > 0 ? q : n1 - 1 - q;
                 const V *row = ring + (size_t)(q % D) * RL + (DIR > 0 ? 0 : 1);
-                // the finisher's first step is 0, so the window of position q < K-1 only
-                // receives previous-line values from position w on: the older ones
-                // (slots jj > q) stay in the stale part
-                const unsigned fm = q >= K - 1 ? freshmask : s_mask[q][lane];
+                const unsigned fm = freshmask;
                 AT acc0 = lane == 0 ? -srhs[i] : AT(0);
                 if (nk <= 8) {
                     // every load is issued before the first multiply-add; the
