@@ -55,8 +55,8 @@ def peaks():
 # 8-chain DFMA loop over 8 CTAs/SM (0.5 of a DFMA per SM per clock at ~1.99 GHz).
 FP64_PEAK_TFLOPS = 1.194
 
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per k_sweep launch, 2D N=512 T=8 FP64
-SWEEP_TRAFFIC_BYTES = 475.8e6
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per k_sweep_line launch, 2D N=512 T=8 FP64
+SWEEP_TRAFFIC_BYTES = 522.7e6
 
 
 class ClockSampler:
@@ -384,9 +384,10 @@ def run_native(args, world, rank, local):
     if dominant == "sweeps":
         dur_s = prof["sweep_us"] / 1e6 / max(1, prof["sweep_calls"])
         # DRAM bytes per sweep launch of this kernel version at this size, from the ncu
-        # capture in profiles/k_sweep_c2_fp64_traffic.md (mean of the forward and backward launch)
+        # capture in profiles/k_sweep_line_c2_fp64_traffic.md (mean of the forward and backward launch)
         traffic = SWEEP_TRAFFIC_BYTES if (d, N, T) == (2, 512, 8) else None
-        roof = dict(kernel="k_sweep (one triangular sweep, Algorithm 3 or 4)", bound="hbm",
+        roof = dict(kernel="k_sweep_line (one triangular sweep, Algorithm 3 or 4; timed with its output fill)",
+                    bound="hbm",
                     achieved=sweep_bytes_total / max(1, prof["sweep_calls"]) / dur_s / 1e9, peak=hbm, unit="GB/s",
                     launches=prof["sweep_calls"], avg_launch_ms=dur_s * 1e3, traffic=traffic,
                     algorithmic_bytes_per_launch=sweep_bytes_total / max(1, prof["sweep_calls"]))
