@@ -638,6 +638,7 @@ constexpr int L1_DT = 32;                // ring of stale results (positions)
 constexpr int L1_WARPS = L1_NS + 5;      // + finisher, TMA producer, two loaders, publisher
 constexpr int L1_D = 32;                 // factor ring depth (rows); rows D further ahead are prefetched to L2
 constexpr int L1_CH = 4;                 // rows per ring barrier (the finisher checks one per L1_CH positions)
+constexpr int L1_DS = 8;                 // ring depth where 32 rows do not fit (3D rows)
 constexpr int L1_KMAX = 8;               // largest fresh window
 
 template <typename AT>
@@ -666,6 +667,13 @@ __device__ __forceinline__ unsigned ld_poll(const float *p)
     asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+// L1-cached read of a value that is written once: a copy that differs from the
+// fill pattern is the final value.
+__device__ __forceinline__ unsigned long long ld_cached(const double *p)
+{
+    return __ldca(reinterpret_cast<const unsigned long long *>(p));
+}
+__device__ __forceinline__ unsigned ld_cached(const float *p) { return __ldca(reinterpret_cast<const unsigned *>(p)); }
 __device__ __forceinline__ void st_final(double *p, double v)
 {
     asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(__double_as_longlong(v)) : "memory");
@@ -723,7 +731,7 @@ __global__ void k_line_fill(AT *out, long long n, unsigned *counter, const int *
 }
 
 struct LineSmem {
-    size_t sy, srhs, sT, ring, mbar, meta, total;
+    size_t sy, srhs, sT, ring, mbar, meta, tab, total;
     int RS, PADL, rows;  // row stride, left padding (elements), value rows (halo + own line)
 };
 
@@ -743,6 +751,8 @@ __host__ __device__ inline LineSmem line_layout(int d, int n1, int w, int D, int
     o = (o + 7) / 8 * 8;
     L.mbar = o; o += (size_t)D * 8;
     L.meta = o; o += (size_t)nslot * 4;
+    o = (o + 7) / 8 * 8;
+    L.tab = o;  o += d == 3 ? (size_t)nslot * 8 : 0;  // 3D: per-line slot table
     L.total = o;
     return L;
 }
@@ -804,6 +814,29 @@ __device__ __forceinline__ bool poll_value(const AT *p, AT &val, const volatile 
     }
     val = Fill<AT>::val(b);
     return __all_sync(0xffffffffu, good);
+}
+
+// Bounded poll of a value of another CTA's line in global memory (final once it
+// differs from the fill pattern); per lane, no warp collectives.
+template <typename AT>
+__device__ __forceinline__ bool poll_global(const AT *p, AT &val, const volatile int *abort_flag, int *err)
+{
+    const long long t0 = clock64();
+    for (int it = 0;; ++it) {
+        const typename Fill<AT>::bits b = ld_poll(p);
+        if (b != Fill<AT>::v) {
+            val = Fill<AT>::val(b);
+            return true;
+        }
+        __nanosleep(32);
+        if ((it & 15) == 15) {
+            if (*abort_flag || *(volatile int *)err != 0) return false;
+            if (clock64() - t0 > kSpinBudgetCycles) {
+                set_err(err, DERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
 }
 
 // Bounded wait for an mbarrier phase that also gives up when the CTA aborts.
@@ -932,7 +965,10 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
         const long long line = DIR > 0 ? v : G.nlines - 1 - v;
         // the finisher polls the values of line v-1 and the stale results for the
         // fill pattern; everything else starts at zero (padding, absent lines)
-        const bool prev_exists = G.d >= 2 && v >= 1;
+        // index of the line within its plane in sweep order: lines of another plane are
+        // no neighbours of this one (3D) and are neither staged nor waited for
+        const long long vin = G.d == 3 ? v % n1 : v;
+        const bool prev_exists = G.d >= 2 && vin >= 1;
         bits_t *ybits = reinterpret_cast<bits_t *>(sy);
         for (int e = threadIdx.x; e < Lo.rows * RS; e += blockDim.x) {
             const int r = e / RS, c = e - r * RS - PADL;
@@ -940,11 +976,36 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
         }
         for (int e = threadIdx.x; e < L1_DT; e += blockDim.x) reinterpret_cast<bits_t *>(sT)[e] = FB::v;
         for (int q = threadIdx.x; q < n1; q += blockDim.x) srhs[q] = rhs[q + (long long)n1 * line];
+        if (G.d == 3) {
+            // the line's slot table: each slot of the stale part that can be in the grid
+            // for some position, with the offset of its value from position i (in the
+            // output relative to this line, or in the row buffers) and dx for the one
+            // check that depends on the position; window slots and slots whose line
+            // is outside the grid are dropped (x = dx + 64 < 0 marks them)
+            const int lj = (int)(line % n1), lk = (int)(line / n1);
+            int2 *tab = reinterpret_cast<int2 *>(smem + Lo.tab);
+            for (int t = threadIdx.x; t < nslot; t += blockDim.x) {
+                const unsigned m = meta[t];
+                const int dx = (int)(m & 255u) - 128, dy = (int)((m >> 8) & 255u) - 128, dz = (int)((m >> 16) & 255u) - 128;
+                const int om = -DIR * dx, oj = w - DIR * dx;
+                const bool win = dz == 0 && ((dy == 0 && om >= 1 && om <= K) || (dy == -DIR && oj >= 0 && oj < K));
+                const int cj = lj + dy, ck = lk + dz;
+                int2 e;
+                if (win || cj < 0 || cj >= n1 || ck < 0 || ck >= n1) {
+                    e = make_int2(0, -1);
+                } else if (dz == 0) {
+                    e = make_int2((own + DIR * dy) * RS + PADL + dx, (dx + 64) | (1 << 8));
+                } else {
+                    e = make_int2(dx + n1 * (dy + n1 * dz), dx + 64);
+                }
+                tab[t] = e;
+            }
+        }
         if (threadIdx.x == 0) {
             // lines before the first one, and lines of 1D problems, do not exist
-            if (G.d < 2 || v < 1) s_near = n1;
-            if (G.d < 2 || v < 2) s_near2 = n1;
-            if (G.d < 2 || v < 3 || w < 3) s_far = n1;
+            if (G.d < 2 || vin < 1) s_near = n1;
+            if (G.d < 2 || vin < 2) s_near2 = n1;
+            if (G.d < 2 || vin < 3 || w < 3) s_far = n1;
         }
         __syncthreads();
         bool ok = true;
@@ -1047,7 +1108,57 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
                 const V *row = ring + (size_t)(q % D) * RL + (DIR > 0 ? 0 : 1);
                 const unsigned fm = freshmask;
                 AT acc0 = lane == 0 ? -srhs[i] : AT(0);
-                if (nk <= 8) {
+                if (G.d == 3) {
+                    // same-plane neighbours from the row buffers, the other planes' values
+                    // straight from the output through L1 (a value is read by 2w+1
+                    // consecutive positions; it is final once it differs from the fill, and
+                    // one that is not yet -- or whose L1 copy predates it -- is polled from
+                    // L2), G3 slots per lane at a time, offsets from the line's slot table
+                    constexpr int G3 = sizeof(AT) == 8 ? 8 : 12;
+                    const int2 *tab = reinterpret_cast<const int2 *>(smem + Lo.tab);
+                    const AT *obase = out + (long long)n1 * line + i;
+                    for (int t0 = lane; t0 - lane < nslot; t0 += 32 * G3) {
+                        AT yv[G3];
+                        V fv[G3];
+                        unsigned pend = 0;
+#pragma unroll
+                        for (int u = 0; u < G3; ++u) {
+                            yv[u] = AT(0);
+                            fv[u] = V(0);
+                            if ((t0 - lane) + 32 * u >= nslot) break;  // warp-uniform
+                            const int t = t0 + 32 * u;
+                            if (t >= nslot) continue;
+                            const int2 e = tab[t];
+                            const int ci = i + (e.y & 255) - 64;
+                            if (e.y < 0 || ci < 0 || ci >= n1) continue;
+                            fv[u] = row[t];
+                            if (e.y >> 8) {
+                                yv[u] = sy[e.x + i];
+                            } else {
+                                const bits_t bb = ld_cached(obase + e.x);
+                                if (bb == FB::v) pend |= 1u << u;
+                                yv[u] = FB::val(bb);
+                            }
+                        }
+                        if (__any_sync(FULL, pend != 0)) {
+                            bool good = true;
+#pragma unroll
+                            for (int u = 0; u < G3; ++u)
+                                if (good && (pend >> u & 1u))
+                                    good = poll_global(obase + tab[t0 + 32 * u].x, yv[u], &s_abort, A.err);
+                            if (!__all_sync(FULL, good)) {
+                                ok = false;
+                                break;
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < G3; ++u) {
+                            if ((t0 - lane) + 32 * u >= nslot) break;  // warp-uniform: no idle FP64 issue
+                            acc0 += (AT)fv[u] * yv[u];
+                        }
+                    }
+                    if (!ok) break;
+                } else if (nk <= 8) {
                     // every load is issued before the first multiply-add; the
                     // multiply-adds stop at a warp-uniform trip count
                     V fv[8];
@@ -1192,7 +1303,7 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
         } else if (role == R_FAR) {
             // ---------------------------------------------------------------- loader: lines v-3 .. v-w
             // lane h holds how far line v-h is staged
-            int my = (G.d >= 2 && lane >= 3 && lane <= w && v - lane >= 0) ? 0 : n1;
+            int my = (G.d >= 2 && lane >= 3 && lane <= w && vin - lane >= 0) ? 0 : n1;
             const long long t0 = clock64();
             for (int itp = 0;; ++itp) {
                 if ((int)__reduce_min_sync(FULL, (unsigned)my) >= n1) break;
@@ -1286,19 +1397,26 @@ static int launch_sweep_d(const SweepArgs &A, int D, size_t smem, unsigned grid,
     return launch_sweep<V, AT, DIR, 4>(A, smem, grid, s);
 }
 
-template <typename V, typename AT, int DIR>
+template <typename V, typename AT, int DIR, int D>
 static int launch_line(const SweepArgs &A, size_t smem, unsigned grid, cudaStream_t s)
 {
     static size_t attr = 0;  // benign race: setting the attribute twice is harmless
     if (smem > attr) {
-        LSG_CK(cudaFuncSetAttribute(k_sweep_line<V, AT, DIR, L1_D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        LSG_CK(cudaFuncSetAttribute(k_sweep_line<V, AT, DIR, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
         attr = smem;
     }
     ::lsg::count_launch();
-    k_sweep_line<V, AT, DIR, L1_D><<<grid, 32 * L1_WARPS, smem, s>>>(A);
+    k_sweep_line<V, AT, DIR, D><<<grid, 32 * L1_WARPS, smem, s>>>(A);
     LSG_CK(cudaGetLastError());
     return LSG_OK;
+}
+
+template <typename V, typename AT, int DIR>
+static int launch_line_d(const SweepArgs &A, int D, size_t smem, unsigned grid, cudaStream_t s)
+{
+    if (D == L1_D) return launch_line<V, AT, DIR, L1_D>(A, smem, grid, s);
+    return launch_line<V, AT, DIR, L1_DS>(A, smem, grid, s);
 }
 
 template <typename AT>
@@ -1313,7 +1431,7 @@ static int launch_fill(AT *out, long long n, unsigned *counter, const int *done,
 
 // Both sweeps with the line-parallel kernel (1D and 2D).
 template <typename V, typename AT>
-static int sweeps_line(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done, cudaStream_t s, size_t smf,
+static int sweeps_line(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done, cudaStream_t s, int D, size_t smf,
                        size_t smb)
 {
     const Geom &g = c->g;
@@ -1323,8 +1441,9 @@ static int sweeps_line(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done
     A.err = c->err;
     A.B = 1;
     // fresh window: the stale part of a row may start K positions before the row
-    // is finished, which covers its ~1 us FP64 reduction at a few hundred ns per position
-    A.K = 8;
+    // is finished, which covers its ~1 us FP64 reduction at a few hundred ns per position;
+    // the ring must hold the window's rows and K more (K <= D - 4)
+    A.K = D >= 16 ? 8 : 4;
     int dev = 0, nsm = 0;
     LSG_CK(cudaGetDevice(&dev));
     LSG_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -1338,7 +1457,7 @@ static int sweeps_line(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done
     A.counter = c->counters + 1;
     LSG_TRY(prof_begin(c, PROF_SWEEP_L, s, &slot));
     LSG_TRY(launch_fill<AT>(ytmp, g.n, c->counters + 1, done, nsm, s));
-    LSG_TRY((launch_line<V, AT, 1>(A, smf, grid, s)));
+    LSG_TRY((launch_line_d<V, AT, 1>(A, D, smf, grid, s)));
     LSG_TRY(prof_end(c, slot, s));
     // backward: U z = y (z is filled only now: it may be the same vector as r)
     A.F = c->Uv;
@@ -1348,7 +1467,7 @@ static int sweeps_line(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done
     A.counter = c->counters + 2;
     LSG_TRY(prof_begin(c, PROF_SWEEP_U, s, &slot));
     LSG_TRY(launch_fill<AT>(z, g.n, c->counters + 2, done, nsm, s));
-    LSG_TRY((launch_line<V, AT, -1>(A, smb, grid, s)));
+    LSG_TRY((launch_line_d<V, AT, -1>(A, D, smb, grid, s)));
     LSG_TRY(prof_end(c, slot, s));
     return LSG_OK;
 }
@@ -1358,11 +1477,13 @@ static int sweeps(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done, cud
 {
     const Geom &g = c->g;
     const size_t budget = 210 * 1024;
-    if (g.d <= 2 && g.Sc <= 32 * SW_KS && g.w <= 31) {
+    if ((g.d == 3 || g.Sc <= 32 * SW_KS) && g.w <= 31) {
         const int vs = (int)sizeof(V), as = (int)sizeof(AT);
-        const size_t smf = line_layout(g.d, g.n1, g.w, L1_D, g.SL, vs, g.Sc, as).total;
-        const size_t smb = line_layout(g.d, g.n1, g.w, L1_D, g.SU, vs, g.Sc, as).total;
-        if (std::max(smf, smb) <= budget) return sweeps_line<V, AT>(c, r, z, ytmp, done, s, smf, smb);
+        for (int D : {L1_D, L1_DS}) {
+            const size_t smf = line_layout(g.d, g.n1, g.w, D, g.SL, vs, g.Sc, as).total;
+            const size_t smb = line_layout(g.d, g.n1, g.w, D, g.SU, vs, g.Sc, as).total;
+            if (std::max(smf, smb) <= budget) return sweeps_line<V, AT>(c, r, z, ytmp, done, s, D, smf, smb);
+        }
     }
     SweepArgs A{};
     A.G = sgeo(g);
