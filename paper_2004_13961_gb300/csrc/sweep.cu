@@ -7,7 +7,12 @@
 // (i+w,j+w,k-1) in 3D).  A line (fixed j,k) is a chain whose position i may
 // be finished once the previous line has finished position i+w.
 //
-// Kernel design (GB300).  A CTA owns a band of B consecutive lines, one
+// Two kernels.  k_sweep_line (further below) runs one line per CTA with the
+// line's work split over warps; it is used whenever its shared-memory layout
+// fits (1D, 2D with up to 512 lower slots per row, 3D).  k_sweep, the band
+// kernel described next, covers the rest (2D stencils wider than that).
+//
+// Band kernel design (GB300).  A CTA owns a band of B consecutive lines, one
 // compute warp per line.  A line warp advances as soon as its inputs exist:
 // it waits only for its predecessor's progress counter in shared memory (the
 // halo loader publishes separate counts for the line before the band and the
@@ -626,16 +631,16 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
 //     multiply-adds and, backward, the multiply by the stored 1 / U(i,i);
 //   * a TMA producer streams the line's factor rows into a ring of D rows;
 //   * two loader warps stage the w lines before this one into shared memory
-//     straight from the output vector, and a publisher warp stores the line's
-//     finished values there.  The output is filled with a signalling NaN before
-//     the sweep and every value is stored once, so a word that differs from the
-//     fill is final: no progress words, no fences.
+//     straight from the output vector, where the finisher stores each value.  The
+//     output is filled with a signalling NaN before the sweep and every value is
+//     stored once, so a word that differs from the fill is final: no progress
+//     words, no fences.
 //     (Arithmetic never produces a signalling NaN.)
 // Lines are claimed in sweep order, so a CTA only waits for lines claimed
 // earlier by running CTAs; every wait is bounded and reports LSG_ERR_TIMEOUT.
 constexpr int L1_NS = 6;                 // stale warps
 constexpr int L1_DT = 32;                // ring of stale results (positions)
-constexpr int L1_WARPS = L1_NS + 5;      // + finisher, TMA producer, two loaders, publisher
+constexpr int L1_WARPS = 11;             // finisher, six stale warps, TMA producer, two loaders, one idle
 constexpr int L1_D = 32;                 // factor ring depth (rows); rows D further ahead are prefetched to L2
 constexpr int L1_CH = 4;                 // rows per ring barrier (the finisher checks one per L1_CH positions)
 constexpr int L1_DS = 8;                 // ring depth where 32 rows do not fit (3D rows)
@@ -885,10 +890,11 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
     __shared__ long long s_line;
     __shared__ int s_issued;                   // chunks the producer issued (this line)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // warp roles: the finisher alone on sub-partition 0 with the producer (no FP64
-    // work), the stale warps two per sub-partition 1-3, the loaders and the publisher
-    enum { R_FIN, R_STALE, R_PROD, R_NEAR, R_FAR, R_PUB };
-    const int role = wid == 0 ? R_FIN : wid == 4 ? R_PROD : wid == 8 ? R_NEAR : wid == 9 ? R_FAR : wid == 10 ? R_PUB
+    // warp roles (warp w runs on SM sub-partition w % 4): the finisher on
+    // sub-partition 0 with only the far loader (mostly idle) and an idle warp; the
+    // stale warps two per sub-partition 1-3 with the producer and the near loader
+    enum { R_FIN, R_STALE, R_PROD, R_NEAR, R_FAR, R_IDLE };
+    const int role = wid == 0 ? R_FIN : wid == 4 ? R_FAR : wid == 8 ? R_IDLE : wid == 9 ? R_PROD : wid == 10 ? R_NEAR
                                                                                                             : R_STALE;
     const int sw = wid < 4 ? wid - 1 : wid - 2;  // stale warp index (R_STALE)
     const AT *rhs = (const AT *)A.rhs;
@@ -1071,27 +1077,40 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
                 if (j >= K - 1) Gw = AT(0);
                 ok = next_operands(s + 1);
             }
-            for (int s = 0; s < n1 && ok; ++s) {
-                const int i = DIR > 0 ? s : n1 - 1 - s;
+            // Bv: the stale part and the previous line's value of the step (lane 0 adds
+            // T_s), computed from operands read one step ahead, off the loop-carried chain
+            AT Bv = 0;
+            auto make_B = [&](int s) -> bool {
                 AT Tv = FB::val(tb), yp = FB::val(pb);
                 if (tb == FB::v || pb == FB::v) {
-                    ok = poll_value(&sT[s % L1_DT], Tv, &s_abort, A.err) &&
-                         (G.d < 2 || poll_value(&sy[prevoff + i], yp, &s_abort, A.err));
-                    if (!ok) break;
+                    if (!(poll_value(&sT[s % L1_DT], Tv, &s_abort, A.err) &&
+                          (G.d < 2 || poll_value(&sy[prevoff + (DIR > 0 ? s : n1 - 1 - s)], yp, &s_abort, A.err))))
+                        return false;
                 }
-                // the stale part and the previous line's value go into a separate
-                // register, off the loop-carried chain (add, multiply-add by y_{s-1})
-                const AT Bv = fma(-fp, yp, (j == 0) ? Tv : AT(0));
+                Bv = fma(-fp, yp, (j == 0) ? Tv : AT(0));
+                return true;
+            };
+            if (ok && n1 > 0) ok = make_B(0);
+            for (int s = 0; s < n1 && ok; ++s) {
+                const int i = DIR > 0 ? s : n1 - 1 - s;
+                // the chain: add, multiply-add by y_{s-1}; the next step's operands are
+                // read while it completes
                 const AT r = fma(-fo, yb, Gw + Bv);
-                yb = __shfl_sync(FULL, DIR < 0 ? r * ri : r, 0);
+                const AT val = DIR < 0 ? r * ri : r;
+                const bool more = s + 1 < n1;
+                if (more) ok = next_operands(s + 1);
+                yb = __shfl_sync(FULL, val, 0);
+                Gw = __shfl_down_sync(FULL, r, 1);
+                if (j >= K - 1) Gw = AT(0);
                 // every lane has read this step's stale slot (the shuffle synchronises
                 // the warp): refill it, then publish y_s (all lanes store the same value)
                 sts_vol(a_T + (unsigned)((s % L1_DT) * (int)sizeof(AT)), FB::v);
                 sts_val(a_Y + (unsigned)(i * (int)sizeof(AT)), yb);
                 st_release_cta(&s_prog, s + 1);
-                Gw = __shfl_down_sync(FULL, r, 1);
-                if (j >= K - 1) Gw = AT(0);
-                if (s + 1 < n1) ok = next_operands(s + 1);
+                // and to the output for the next lines (after the release: its fence does
+                // not wait for this store)
+                if (lane == 0) st_final(out + i + (long long)n1 * line, yb);
+                if (ok && more) ok = make_B(s + 1);
             }
         } else if (role == R_STALE) {
             // ---------------------------------------------------------------- stale warps
@@ -1258,37 +1277,6 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
                     if (itp > 64) __nanosleep(32);
                     if ((itp & 15) == 15) {
                         bool stop = s_abort != 0 || *(volatile int *)A.err != 0;
-                        if (clock64() - t0 > 4 * kSpinBudgetCycles) {
-                            if (lane == 0) set_err(A.err, DERR_TIMEOUT);
-                            stop = true;
-                        }
-                        if (__any_sync(FULL, stop)) {
-                            ok = false;
-                            break;
-                        }
-                    }
-                }
-            }
-        } else if (role == R_PUB) {
-            // ---------------------------------------------------------------- publisher
-            // stores finished values to the output (the finisher touches shared memory
-            // only, so no fence of its waits on a global store)
-            const AT *yrow = sy + own * RS + PADL;
-            AT *oline = out + (long long)n1 * line;
-            int pub = 0;
-            const long long t0 = clock64();
-            for (int itp = 0; pub < n1; ++itp) {
-                const int fin = ld_acquire_cta(&s_prog);
-                if (fin > pub) {
-                    for (int p = pub + lane; p < fin; p += 32) {
-                        const int i = DIR > 0 ? p : n1 - 1 - p;
-                        st_final(oline + i, yrow[i]);
-                    }
-                    pub = fin;
-                } else {
-                    if (itp > 64) __nanosleep(16);
-                    if ((itp & 15) == 15) {
-                        bool stop = s_abort != 0;
                         if (clock64() - t0 > 4 * kSpinBudgetCycles) {
                             if (lane == 0) set_err(A.err, DERR_TIMEOUT);
                             stop = true;
