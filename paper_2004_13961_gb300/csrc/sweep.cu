@@ -645,6 +645,7 @@ constexpr int L1_D = 32;                 // factor ring depth (rows); rows D fur
 constexpr int L1_CH = 4;                 // rows per ring barrier (the finisher checks one per L1_CH positions)
 constexpr int L1_DS = 8;                 // ring depth where 32 rows do not fit (3D rows)
 constexpr int L1_KMAX = 8;               // largest fresh window
+constexpr int L1_FB = 16;                // finisher steps per block (ring waits at block starts)
 
 template <typename AT>
 struct Fill;
@@ -842,6 +843,20 @@ __device__ __forceinline__ bool poll_global(const AT *p, AT &val, const volatile
             }
         }
     }
+}
+
+// The finisher's rare slow path: poll the stale part and (2D/3D) the previous
+// line's value until both are final.  Kept out of line so that the step loop
+// holds no loop of its own.
+template <typename AT>
+__device__ __noinline__ bool poll_operands(const AT *pT, const AT *pP, AT *Tv, AT *yp, const volatile int *abort_flag,
+                                           int *err)
+{
+    AT a, b = AT(0);
+    const bool good = poll_value(pT, a, abort_flag, err) && (pP == nullptr || poll_value(pP, b, abort_flag, err));
+    *Tv = a;
+    if (pP != nullptr) *yp = b;
+    return good;
 }
 
 // Bounded wait for an mbarrier phase that also gives up when the CTA aborts.
@@ -1058,16 +1073,25 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
                            : bits_t(0);
             };
             bits_t tb = 0, pb = 0;
-            auto next_operands = [&](int s) -> bool {  // for step s: the entering row's chunk, then loads
-                const int qn = s + K - 1;
-                if (qn > 0 && qn < n1 && qn % L1_CH == 0 && !wait_chunk(it, qn)) return false;
+            auto next_operands = [&](int s) {  // the window's factors, the stale part, the previous line's value
                 load_factors(s);
                 tb = load_T(s);
                 pb = load_P(s);
-                return true;
             };
-            if (ok) ok = next_operands(s0);
+            // ring chunks the finisher has waited for: rows [0, rows_ok) have landed
+            int rows_ok = 0;
+            auto need_rows = [&](int upto) -> bool {  // wait for the chunks of rows < upto
+                upto = min(upto, n1);
+                bool good = true;
+                while (good && rows_ok < upto) {
+                    good = wait_chunk(it, rows_ok);
+                    rows_ok += L1_CH;
+                }
+                return good;
+            };
             // steps before position 0: previous-line values only
+            ok = ok && need_rows(K);
+            if (ok) next_operands(s0);
             for (int s = s0; s < 0 && ok; ++s) {
                 AT yp = FB::val(pb);
                 if (pb == FB::v) ok = poll_value(&sy[prevoff + (DIR > 0 ? s : n1 - 1 - s)], yp, &s_abort, A.err);
@@ -1075,42 +1099,52 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
                 const AT r = fma(-fp, yp, Gw);
                 Gw = __shfl_down_sync(FULL, r, 1);
                 if (j >= K - 1) Gw = AT(0);
-                ok = next_operands(s + 1);
+                next_operands(s + 1);
             }
             // Bv: the stale part and the previous line's value of the step (lane 0 adds
-            // T_s), computed from operands read one step ahead, off the loop-carried chain
+            // T_s), computed from operands read one step ahead, off the loop-carried chain;
+            // an operand that is not final yet (rare) is polled outside the hot loop's code
             AT Bv = 0;
             auto make_B = [&](int s) -> bool {
                 AT Tv = FB::val(tb), yp = FB::val(pb);
-                if (tb == FB::v || pb == FB::v) {
-                    if (!(poll_value(&sT[s % L1_DT], Tv, &s_abort, A.err) &&
-                          (G.d < 2 || poll_value(&sy[prevoff + (DIR > 0 ? s : n1 - 1 - s)], yp, &s_abort, A.err))))
+                if (__any_sync(FULL, tb == FB::v || pb == FB::v)) {
+                    if (!poll_operands(&sT[s % L1_DT], G.d >= 2 ? &sy[prevoff + (DIR > 0 ? s : n1 - 1 - s)] : nullptr,
+                                       &Tv, &yp, &s_abort, A.err))
                         return false;
                 }
                 Bv = fma(-fp, yp, (j == 0) ? Tv : AT(0));
                 return true;
             };
             if (ok && n1 > 0) ok = make_B(0);
-            for (int s = 0; s < n1 && ok; ++s) {
-                const int i = DIR > 0 ? s : n1 - 1 - s;
-                // the chain: add, multiply-add by y_{s-1}; the next step's operands are
-                // read while it completes
-                const AT r = fma(-fo, yb, Gw + Bv);
-                const AT val = DIR < 0 ? r * ri : r;
-                const bool more = s + 1 < n1;
-                if (more) ok = next_operands(s + 1);
-                yb = __shfl_sync(FULL, val, 0);
-                Gw = __shfl_down_sync(FULL, r, 1);
-                if (j >= K - 1) Gw = AT(0);
-                // every lane has read this step's stale slot (the shuffle synchronises
-                // the warp): refill it, then publish y_s (all lanes store the same value)
-                sts_vol(a_T + (unsigned)((s % L1_DT) * (int)sizeof(AT)), FB::v);
-                sts_val(a_Y + (unsigned)(i * (int)sizeof(AT)), yb);
-                st_release_cta(&s_prog, s + 1);
-                // and to the output for the next lines (after the release: its fence does
-                // not wait for this store)
-                if (lane == 0) st_final(out + i + (long long)n1 * line, yb);
-                if (ok && more) ok = make_B(s + 1);
+            // blocks of fb steps: the ring chunks a block reads (its windows and the next
+            // step's operands: rows < sb + fb + K) are waited for at its start, so that the
+            // steps themselves carry no such branch; the ring holds rows up to D-1 past the
+            // finisher's position, hence fb <= D - K
+            const int fb = min(L1_FB, D - K);
+            for (int sb = 0; sb < n1 && ok; sb += fb) {
+                ok = need_rows(sb + fb + K);
+                const int se = min(sb + fb, n1);
+                for (int s = sb; s < se && ok; ++s) {
+                    const int i = DIR > 0 ? s : n1 - 1 - s;
+                    // the chain: add, multiply-add by y_{s-1}; the next step's operands are
+                    // read while it completes
+                    const AT r = fma(-fo, yb, Gw + Bv);
+                    const AT val = DIR < 0 ? r * ri : r;
+                    const bool more = s + 1 < n1;
+                    if (more) next_operands(s + 1);
+                    yb = __shfl_sync(FULL, val, 0);
+                    Gw = __shfl_down_sync(FULL, r, 1);
+                    if (j >= K - 1) Gw = AT(0);
+                    // every lane has read this step's stale slot (the shuffle synchronises
+                    // the warp): refill it, then publish y_s (all lanes store the same value)
+                    sts_vol(a_T + (unsigned)((s % L1_DT) * (int)sizeof(AT)), FB::v);
+                    sts_val(a_Y + (unsigned)(i * (int)sizeof(AT)), yb);
+                    st_release_cta(&s_prog, s + 1);
+                    // and to the output for the next lines (after the release: its fence does
+                    // not wait for this store)
+                    if (lane == 0) st_final(out + i + (long long)n1 * line, yb);
+                    if (more) ok = make_B(s + 1);
+                }
             }
         } else if (role == R_STALE) {
             // ---------------------------------------------------------------- stale warps
