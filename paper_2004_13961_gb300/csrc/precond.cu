@@ -170,7 +170,7 @@ __global__ void k_level_scatter(StencilGeo G, int *cursor, int *order)
 constexpr int ILU_MAX_WARPS = 8;
 
 struct IluSmem {
-    size_t off, smask, warps, per_warp, total;
+    size_t off, smask, ord, warps, per_warp, total;
 };
 __host__ __device__ inline size_t al16(size_t b) { return (b + 15) / 16 * 16; }
 __host__ __device__ inline IluSmem ilu_layout(int S, int SU, int D, int vsize, int nw)
@@ -178,7 +178,8 @@ __host__ __device__ inline IluSmem ilu_layout(int S, int SU, int D, int vsize, i
     IluSmem L;
     L.off = 0;
     L.smask = al16((size_t)S * 4);
-    L.warps = L.smask + al16((size_t)S);
+    L.ord = L.smask + al16((size_t)S);
+    L.warps = L.ord + al16((size_t)S * 2);
     L.per_warp = al16((size_t)S * vsize) + (size_t)D * SU * vsize;
     L.total = L.warps + (size_t)nw * L.per_warp;
     return L;
@@ -202,18 +203,17 @@ __device__ __forceinline__ void ilu_off(int m, int &dx, int &dy, int &dz)
     dz = ((m >> 16) & 255) - 128;
 }
 
-// first lower slot >= s of row (i,j,k) whose column is in the grid and in the pattern
-__device__ __forceinline__ int ilu_next(const StencilGeo &G, const int *off, const unsigned char *smask, int s,
-                                        int i, int j, int k)
+// first position >= p of the step order whose slot's column is in the grid of row (i,j,k)
+__device__ __forceinline__ int ilu_next(const StencilGeo &G, const int *off, const short *ord, int nord, int p, int i,
+                                        int j, int k)
 {
-    for (; s < G.Sc; ++s) {
-        if (!smask[s]) continue;
+    for (; p < nord; ++p) {
         int dx, dy, dz;
-        ilu_off(off[s], dx, dy, dz);
+        ilu_off(off[ord[p]], dx, dy, dz);
         const int ci = i + dx, cj = j + dy, ck = k + dz;
-        if (ci >= 0 && ci < G.n1 && cj >= 0 && cj < G.n1 && ck >= 0 && ck < G.n1) return s;
+        if (ci >= 0 && ci < G.n1 && cj >= 0 && cj < G.n1 && ck >= 0 && ck < G.n1) return p;
     }
-    return G.Sc;
+    return nord;
 }
 
 __device__ __forceinline__ long long ilu_row_of(const StencilGeo &G, long long r, int m)
@@ -242,6 +242,7 @@ __global__ void __launch_bounds__(32 * ILU_MAX_WARPS, 2) k_ilu0(StencilGeo G, V 
     const IluSmem Lo = ilu_layout(S, SU, D, (int)sizeof(V), nw);
     int *off = (int *)(smem + Lo.off);           // offset (dx,dy,dz) of every slot, biased bytes
     unsigned char *smask = smem + Lo.smask;      // structural flag per slot
+    short *ord = (short *)(smem + Lo.ord);       // the step order: structural lower slots
     V *a = (V *)(smem + Lo.warps + (size_t)wid * Lo.per_warp);
     V *ring = (V *)((unsigned char *)a + al16((size_t)S * sizeof(V)));
     for (int t = threadIdx.x; t < S; t += blockDim.x) {
@@ -251,6 +252,37 @@ __global__ void __launch_bounds__(32 * ILU_MAX_WARPS, 2) k_ilu0(StencilGeo G, V 
         smask[t] = structural(G, dx, dy, dz) ? 1 : 0;
     }
     __syncthreads();
+    // Step order.  Step k can change H(r,k') only if k' - k is an upper offset in the
+    // box, and such an offset raises the wavefront level i + (w+1) j + (w+1)^2 k by at
+    // least one; so taking the lower slots by increasing level (then column) is a
+    // valid elimination order, and it leaves the steps on the rows of the previous
+    // level (the last to finish) for the end: two of them in 2D, three in 3D, where
+    // column order would leave w+1.  The result is the same; only the order in which
+    // the updates of each entry are added differs.
+    auto lev = [&](int t) {
+        int dx, dy, dz;
+        ilu_off(off[t], dx, dy, dz);
+        return dx + (G.w + 1) * (dy + (G.w + 1) * dz);
+    };
+    for (int t = threadIdx.x; t < Sc; t += blockDim.x) {
+        if (!smask[t]) continue;
+        const int lt = lev(t);
+        int rank = 0;
+        for (int u = 0; u < Sc; ++u) {
+            if (!smask[u]) continue;
+            const int lu = lev(u);
+            rank += (lu < lt || (lu == lt && u < t)) ? 1 : 0;
+        }
+        ord[rank] = (short)t;
+    }
+    __shared__ int s_nord;
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int t = 0; t < Sc; ++t) c += smask[t];
+        s_nord = c;
+    }
+    __syncthreads();
+    const int nord = s_nord;
 
     for (;;) {
         long long idx = 0;
@@ -270,11 +302,11 @@ __global__ void __launch_bounds__(32 * ILU_MAX_WARPS, 2) k_ilu0(StencilGeo G, V 
         // producer cursor ps: the next step whose U row goes to ring slot pq; bit q of
         // `ready` says whether slot q holds its step's row (prefetched) or must be
         // fetched when consumed (its row was not finished at prefetch time)
-        int ps = ilu_next(G, off, smask, 0, i, j, k), pq = 0;
+        int ps = ilu_next(G, off, ord, nord, 0, i, j, k), pq = 0;
         unsigned ready = 0;
         auto prefetch = [&]() {
-            if (ps < Sc) {
-                const long long kr = ilu_row_of(G, r, off[ps]);
+            if (ps < nord) {
+                const long long kr = ilu_row_of(G, r, off[ord[ps]]);
                 unsigned f = 0;
                 if (lane == 0) f = ld_acquire(rowflag + kr);
                 f = __shfl_sync(0xffffffffu, f, 0);
@@ -285,16 +317,17 @@ __global__ void __launch_bounds__(32 * ILU_MAX_WARPS, 2) k_ilu0(StencilGeo G, V 
                 } else {
                     ready &= ~(1u << pq);
                 }
-                ps = ilu_next(G, off, smask, ps + 1, i, j, k);
+                ps = ilu_next(G, off, ord, nord, ps + 1, i, j, k);
                 pq = (pq + 1 == D) ? 0 : pq + 1;
             }
             ilu_commit();
         };
 #pragma unroll 1
         for (int q = 0; q < D - 1; ++q) prefetch();
-        int cs = ilu_next(G, off, smask, 0, i, j, k), q = 0;
+        int cp = ilu_next(G, off, ord, nord, 0, i, j, k), q = 0;
         bool ok = true;
-        while (cs < Sc) {
+        while (cp < nord) {
+            const int cs = ord[cp];
             prefetch();  // step cs + D - 1 into the slot freed by the previous step
             ilu_wait<D - 1>();
             V *Uk = ring + (size_t)q * SU;
@@ -350,7 +383,7 @@ __global__ void __launch_bounds__(32 * ILU_MAX_WARPS, 2) k_ilu0(StencilGeo G, V 
             __syncwarp();
             if (lane == 0) a[cs] = l;
             q = (q + 1 == D) ? 0 : q + 1;
-            cs = ilu_next(G, off, smask, cs + 1, i, j, k);
+            cp = ilu_next(G, off, ord, nord, cp + 1, i, j, k);
         }
         ilu_wait<0>();
         __syncwarp();
