@@ -390,12 +390,14 @@ __global__ void __launch_bounds__(32 * ILU_MAX_WARPS, 2) k_ilu0(StencilGeo G, V 
         if (!ok) return;  // a wait gave up: the error word is set, other warps stop too
         const V uii = a[Sc];
         if (lane == 0 && !((double)uii > 1e-14 * fabs((double)mii))) set_err(err, DERR_BREAKDOWN);
-        for (int t = lane; t < Sc; t += 32) Lv[r * G.SL + t] = a[t];
+        // the U row (all that later rows read) is published first; the L row only
+        // matters to the sweeps, after this kernel
         for (int u = lane; u < nU; u += 32) Uv[r * SU + u] = a[Sc + u];
         if (lane == 0) Uv[r * SU + SU - 1] = V(1) / uii;
         __threadfence();
         __syncwarp();
         if (lane == 0) st_release(rowflag + r, 1u);
+        for (int t = lane; t < Sc; t += 32) Lv[r * G.SL + t] = a[t];
     }
 }
 
