@@ -179,7 +179,7 @@ __host__ __device__ inline IluSmem ilu_layout(int S, int SU, int D, int vsize, i
     L.off = 0;
     L.smask = al16((size_t)S * 4);
     L.ord = L.smask + al16((size_t)S);
-    L.warps = L.ord + al16((size_t)S * 2);
+    L.warps = L.ord + al16((size_t)(S - 1) / 2 * 2);  // Sc step-order entries
     L.per_warp = al16((size_t)S * vsize) + (size_t)D * SU * vsize;
     L.total = L.warps + (size_t)nw * L.per_warp;
     return L;
@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(32 * ILU_MAX_WARPS, 2) k_ilu0(StencilGeo G, V 
 template <typename V, int D>
 static int launch_ilu0_d(lsg_ctx *c, const StencilGeo &G, int nsm, cudaStream_t s)
 {
-    const size_t budget = 200 * 1024;
+    const size_t budget = 224 * 1024;  // of the 227 KB a CTA may opt in to
     const IluSmem one = ilu_layout(G.S, G.SU, D, (int)sizeof(V), 1);
     if (one.total > budget) return LSG_ERR_ARG;  // stencil too wide for a shared-memory row
     int nw = (int)std::min<size_t>(ILU_MAX_WARPS, 1 + (budget - one.total) / one.per_warp);
