@@ -56,7 +56,7 @@ def peaks():
 FP64_PEAK_TFLOPS = 1.194
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per k_sweep_line launch, 2D N=512 T=8 FP64
-SWEEP_TRAFFIC_BYTES = 522.7e6
+SWEEP_TRAFFIC_BYTES = 522.6e6
 
 
 class ClockSampler:
