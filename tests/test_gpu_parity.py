@@ -47,6 +47,7 @@ CASES = [
     (2, 20, 0, 2, False),    # T = 0 and b == 0: even offsets only, rows of a line finish out of order
     (2, 96, 8, 2, True),     # many wavefront levels and warps in flight
     (3, 12, 4, 2, True),     # 3D rows of 1,098 slots: FP64 sweeps with an 8-row ring and window 4
+    (2, 40, 14, 2, True),    # 544 lower slots per row: the band sweep kernel (wider than the line kernel's)
 ]
 
 
