@@ -180,7 +180,8 @@ __host__ __device__ inline IluSmem ilu_layout(int S, int SU, int D, int vsize, i
     L.smask = al16((size_t)S * 4);
     L.ord = L.smask + al16((size_t)S);
     L.warps = L.ord + al16((size_t)(S - 1) / 2 * 2);  // Sc step-order entries
-    L.per_warp = al16((size_t)S * vsize) + (size_t)D * SU * vsize;
+    // the row, the U-row ring, and one bit per step: its row had finished when this row started
+    L.per_warp = al16((size_t)S * vsize) + (size_t)D * SU * vsize + al16(((size_t)(S - 1) / 2 + 31) / 32 * 4);
     L.total = L.warps + (size_t)nw * L.per_warp;
     return L;
 }
@@ -192,6 +193,12 @@ __device__ __forceinline__ void ilu_cp16(void *sdst, const void *gsrc)
                  : "memory");
 }
 __device__ __forceinline__ void ilu_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 template <int N>
 __device__ __forceinline__ void ilu_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
@@ -296,6 +303,31 @@ __global__ void __launch_bounds__(32 * ILU_MAX_WARPS, 2) k_ilu0(StencilGeo G, V 
         const int k = (G.d == 3) ? (int)(r / ((long long)G.n1 * G.n1)) : 0;
         for (int t = lane; t < Sc; t += 32) a[t] = Lv[r * G.SL + t];
         for (int u = lane; u < nU; u += 32) a[Sc + u] = Uv[r * SU + u];
+        // which of the rows this row uses had finished already (most of them: rows are
+        // claimed well ahead of the wavefront): their flags, read by all lanes at once
+        // (relaxed reads, then one fence), spare the per-step check below
+        unsigned *done = (unsigned *)((unsigned char *)ring + (size_t)D * SU * sizeof(V));
+        for (int p0 = 0; p0 < nord; p0 += 4 * 32) {
+            unsigned fl[4];
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                const int p = p0 + 32 * g + lane;
+                fl[g] = 0;
+                if (p < nord) {
+                    int dx, dy, dz;
+                    ilu_off(off[ord[p]], dx, dy, dz);
+                    const int ci = i + dx, cj = j + dy, ck = k + dz;
+                    if (ci >= 0 && ci < G.n1 && cj >= 0 && cj < G.n1 && ck >= 0 && ck < G.n1)
+                        fl[g] = ld_relaxed_u32(rowflag + r + dx + (long long)G.n1 * (dy + (long long)G.n1 * dz));
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                const unsigned m = __ballot_sync(0xffffffffu, fl[g] != 0);
+                if (lane == 0 && p0 + 32 * g < nord) done[(p0 >> 5) + g] = m;
+            }
+        }
+        __threadfence();
         __syncwarp();
         const V mii = a[Sc];
 
@@ -307,9 +339,11 @@ __global__ void __launch_bounds__(32 * ILU_MAX_WARPS, 2) k_ilu0(StencilGeo G, V 
         auto prefetch = [&]() {
             if (ps < nord) {
                 const long long kr = ilu_row_of(G, r, off[ord[ps]]);
-                unsigned f = 0;
-                if (lane == 0) f = ld_acquire(rowflag + kr);
-                f = __shfl_sync(0xffffffffu, f, 0);
+                unsigned f = (done[ps >> 5] >> (ps & 31)) & 1u;
+                if (!f) {
+                    if (lane == 0) f = ld_acquire(rowflag + kr);
+                    f = __shfl_sync(0xffffffffu, f, 0);
+                }
                 __syncwarp();
                 if (f) {
                     ilu_copy_row<V>(G, Uv, kr, ring + (size_t)pq * SU);
