@@ -9,8 +9,9 @@
 //
 // Two kernels.  k_sweep_line (further below) runs one line per CTA with the
 // line's work split over warps; it is used whenever its shared-memory layout
-// fits (1D, 2D with up to 512 lower slots per row, 3D).  k_sweep, the band
-// kernel described next, covers the rest (2D stencils wider than that).
+// fits (1D, 2D with up to 512 lower slots per row, 3D with a ring of at least
+// 8 rows).  k_sweep, the band kernel described next, covers the rest (wider 2D
+// stencils, 3D rows too long for that ring).
 //
 // Band kernel design (GB300).  A CTA owns a band of B consecutive lines, one
 // compute warp per line.  A line warp advances as soon as its inputs exist:
@@ -106,10 +107,6 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void prefetch_l2(const void *gsrc, unsigned bytes)
 {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gsrc), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void named_barrier(int id, int threads)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
 // Bounded wait for an mbarrier phase (every lane polls, so each gets acquire order).
@@ -614,8 +611,8 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
 }
 
 // ============================================================================
-// Line-parallel sweep (1D and 2D): one line per CTA, a position's work split
-// over warps.
+// Line-parallel sweep (1D, 2D and 3D): one line per CTA, a position's work
+// split over warps.
 //
 // In k_sweep the warp of a line computes each row's whole dot product between
 // two of its positions, so a position costs a full FP64 reduction (~1 us) and a
@@ -630,12 +627,13 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
 //     multiply-add, so finishing a position is one addition (T_s), two
 //     multiply-adds and, backward, the multiply by the stored 1 / U(i,i);
 //   * a TMA producer streams the line's factor rows into a ring of D rows;
-//   * two loader warps stage the w lines before this one into shared memory
-//     straight from the output vector, where the finisher stores each value.  The
-//     output is filled with a signalling NaN before the sweep and every value is
-//     stored once, so a word that differs from the fill is final: no progress
-//     words, no fences.
-//     (Arithmetic never produces a signalling NaN.)
+//   * two loader warps stage the w lines before this one (of its own plane, in
+//     3D) into shared memory straight from the output vector, where the
+//     finisher stores each value.  The output is filled with a signalling NaN
+//     before the sweep and every value is stored once, so a word that differs
+//     from the fill is final: no progress words, no fences.  (Arithmetic never
+//     produces a signalling NaN.)  In 3D the stale warps read the other planes'
+//     values from the output the same way, through L1.
 // Lines are claimed in sweep order, so a CTA only waits for lines claimed
 // earlier by running CTAs; every wait is bounded and reports LSG_ERR_TIMEOUT.
 constexpr int L1_NS = 6;                 // stale warps
@@ -644,7 +642,6 @@ constexpr int L1_WARPS = 11;             // finisher, six stale warps, TMA produ
 constexpr int L1_D = 32;                 // factor ring depth (rows); rows D further ahead are prefetched to L2
 constexpr int L1_CH = 4;                 // rows per ring barrier (the finisher checks one per L1_CH positions)
 constexpr int L1_DS = 8;                 // ring depth where 32 rows do not fit (3D rows)
-constexpr int L1_KMAX = 8;               // largest fresh window
 constexpr int L1_FB = 16;                // finisher steps per block (ring waits at block starts)
 
 template <typename AT>
