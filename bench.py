@@ -55,8 +55,19 @@ def peaks():
 # 8-chain DFMA loop over 8 CTAs/SM (0.5 of a DFMA per SM per clock at ~1.99 GHz).
 FP64_PEAK_TFLOPS = 1.194
 
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per k_sweep_line launch, 2D N=512 T=8 FP64
-SWEEP_TRAFFIC_BYTES = 522.6e6
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per k_sweep_line launch (mean of the forward
+# and backward sweep), 2D N=512 T=8 FP64, and the SHA-256 prefix of the sweep sources the counters
+# were taken on: the figure is reported only while the kernel source is unchanged.
+SWEEP_TRAFFIC = dict(bytes=None, source_sha=None)
+
+
+def sweep_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for fn in ("sweep.cu", "stencil.cuh"):
+        with open(os.path.join(ROOT, "paper_2004_13961_gb300", "csrc", fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 class ClockSampler:
@@ -138,32 +149,20 @@ def max_over_ranks(v, world):
 
 # --------------------------------------------------------------------------- oracle (CPU) leg
 
-def oracle_sample(p, iters_hint=None):
-    """Time the CPU oracle on a bounded sample of the workload: the full setup
-    (truncated series, M assembly, ILU(0)) plus two K x and two ILU solves at full
-    size; a solve is extrapolated as setup + iters x (K x + M^-1 r + vector ops)."""
+def oracle_solve(p, rtol=RTOL):
+    """One complete solve by the CPU oracle, timed: setup (truncated series, band matrices,
+    M assembly, ILU(0) of Algorithm 2), the load vector by quadrature, and PCG (Algorithm 1)
+    to the relative residual rtol -- the same steps the GPU step times."""
     import oracle as O
     d, N, T, Q = p["d"], p["N"], p["T"], p["Q"]
     t0 = time.perf_counter()
-    ah = O.coef_trunc(d, Q, T, p["a"])
-    bh = O.coef_trunc(d, Q, T, p["b"])
-    M = O.assemble_M(d, N, T, ah, bh, O.has_b(p["b"]))
-    LU, rc = O.ilu0(M)
-    t_setup = time.perf_counter() - t0
     F = O.load_vector(d, N, Q, p["f"])
-    x = np.random.default_rng(0).standard_normal(len(F))
-    t0 = time.perf_counter()
-    for _ in range(2):
-        O.apply_K(d, N, Q, p["a"], p["b"], x)
-    t_kx = (time.perf_counter() - t0) / 2
-    t0 = time.perf_counter()
-    for _ in range(2):
-        O.ilu_solve(LU, x)
-    t_minv = (time.perf_counter() - t0) / 2
-    iters = iters_hint if iters_hint else 39
-    t_solve = t_setup + iters * (t_kx + t_minv)
-    return dict(t_setup=t_setup, t_kx=t_kx, t_minv=t_minv, iters=iters, t_solve=t_solve,
-                sample_s=t_setup + 2 * (t_kx + t_minv))
+    st = O.setup(d, N, Q, T, p["a"], p["b"])
+    t1 = time.perf_counter()
+    out = O.pcg(d, N, Q, p["a"], p["b"], st["LU"], F, eps=rtol)
+    t2 = time.perf_counter()
+    return dict(t_setup=t1 - t0, t_pcg=t2 - t1, t_solve=t2 - t0, iters=out["iters"], x=out["x"],
+                relres_true=out["relres_true"], status=out["status"])
 
 
 def cores():
@@ -174,23 +173,26 @@ def cores():
 
 
 def run_reference(args, world, rank):
+    """The oracle on the host cores: every step (warm-up and timed) is one complete oracle solve
+    of the workload (setup, load vector, PCG to 1e-12), timed with the host clock."""
     from paper_2004_13961_gb300 import workloads as W
     if rank != 0:
         return
+    import oracle as O
+    O.build()
     p = W.exp_2d_n512()
-    for _ in range(args.warmup if args.warmup < 1 else 0):
-        pass
-    times = []
-    info = None
-    for _ in range(max(1, args.steps)):
-        info = oracle_sample(p)
-        times.append(info["t_solve"])
+    for _ in range(args.warmup):
+        oracle_solve(p)
+    times, last = [], None
+    for _ in range(args.steps):
+        last = oracle_solve(p)
+        times.append(last["t_solve"])
     t = float(np.mean(times))
     value = 1.0 / t
     cb = dict(value=value, unit="solves/s", cores=cores(), kind="oracle",
-              sample=(f"per step: full oracle setup ({info['t_setup']:.1f} s: truncated series, M assembly, "
-                      f"ILU(0)) + 2 K x ({info['t_kx']:.2f} s each) + 2 ILU solves ({info['t_minv']:.2f} s each) "
-                      f"at N=512; solve = setup + {info['iters']} x (K x + M^-1 r)"))
+              sample=(f"per step one complete oracle solve at N=512: setup {last['t_setup']:.1f} s (truncated "
+                      f"series, M assembly, ILU(0)), PCG {last['t_pcg']:.1f} s ({last['iters']} iterations to "
+                      f"1e-12); mean of {args.steps} timed solves after {args.warmup} warm-up solves"))
     line = dict(metric=METRIC, value=value, unit="solves/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=t * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
                 data="synthetic", impl="reference", config=dict(workload=WORKLOAD),
@@ -383,13 +385,15 @@ def run_native(args, world, rank, local):
     dominant = max(stage_ms, key=stage_ms.get)
     if dominant == "sweeps":
         dur_s = prof["sweep_us"] / 1e6 / max(1, prof["sweep_calls"])
-        # DRAM bytes per sweep launch of this kernel version at this size, from the ncu
-        # capture in profiles/k_sweep_line_c2_fp64_traffic.md (mean of the forward and backward launch)
-        traffic = SWEEP_TRAFFIC_BYTES if (d, N, T) == (2, 512, 8) else None
+        # DRAM bytes per sweep launch measured by ncu on this workload, valid only for the
+        # sweep source it was taken on
+        traffic = (SWEEP_TRAFFIC["bytes"] if (d, N, T) == (2, 512, 8)
+                   and SWEEP_TRAFFIC["source_sha"] == sweep_source_sha() else None)
         roof = dict(kernel="k_sweep_line (one triangular sweep, Algorithm 3 or 4; timed with its output fill)",
                     bound="hbm",
                     achieved=sweep_bytes_total / max(1, prof["sweep_calls"]) / dur_s / 1e9, peak=hbm, unit="GB/s",
                     launches=prof["sweep_calls"], avg_launch_ms=dur_s * 1e3, traffic=traffic,
+                    check_minv_half_ms=t_minv / 2,
                     algorithmic_bytes_per_launch=sweep_bytes_total / max(1, prof["sweep_calls"]))
     elif dominant == "kx":
         dur_s = prof["kx_us"] / 1e6 / max(1, prof["kx_calls"])
@@ -403,12 +407,13 @@ def run_native(args, world, rank, local):
         roof["frac"] = roof["achieved"] / roof["peak"]
     roof["peak_source"] = ("of measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if psrc == "measured"
                            else "of fallback") if roof["bound"] == "hbm" else "of measured FP64 FMA loop"
-    roof["timing"] = "CUDA events on the launching stream around every launch of the timed steps"
+    roof["timing"] = ("CUDA events on the launching stream around every launch of the timed steps that did "
+                      "work (launches queued after the stop test return at once and are not counted)")
     iters = info["iters"]
     per_solve = {k + "_ms": v / args.steps for k, v in stage_ms.items()}
 
     # ---- mixed precision: inner FP32 PCG (FP32 ILU factors, FP32 transforms) in FP64 refinement ----
-    mixed = {}
+    mixed, mixed_u = {}, {}
     if not args.no_mixed:
         u64 = u.clone()
         for name, prec in (("tf32", lsg.MIXED_TF32), ("bf16", lsg.MIXED_BF16)):
@@ -440,6 +445,7 @@ def run_native(args, world, rank, local):
                 torch.cuda.synchronize()
                 ms.append(s0.elapsed_time(s1))
             inf = res["info"]
+            mixed_u[name] = um.cpu().numpy()
             err = float(torch.linalg.norm(um - u64) / torch.linalg.norm(u64))
             mixed[name] = dict(solves_s=world * 1e3 / max_over_ranks(float(np.mean(ms)), world),
                                ms_per_solve=float(np.mean(ms)), rtol=1e-10, relres_true=inf["relres_true"],
@@ -474,10 +480,16 @@ def run_native(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        s = oracle_sample(p, iters)
-        cpu = dict(value=1.0 / s["t_solve"], unit="solves/s", cores=cores(), kind="oracle",
-                   sample=(f"full oracle setup ({s['t_setup']:.1f} s) + 2 K x ({s['t_kx']:.2f} s each) + 2 ILU "
-                           f"solves ({s['t_minv']:.2f} s each) at N=512; solve = setup + {iters} x (K x + M^-1 r)"))
+        o = oracle_solve(p)
+        cpu = dict(value=1.0 / o["t_solve"], unit="solves/s", cores=cores(), kind="oracle",
+                   sample=(f"one complete oracle solve at N=512: setup {o['t_setup']:.1f} s (load vector, truncated "
+                           f"series, M assembly, ILU(0)), PCG {o['t_pcg']:.1f} s ({o['iters']} iterations to 1e-12)"),
+                   iters=o["iters"])
+        # the GPU results against the FP64 oracle's solution of the same problem
+        xo = o["x"]
+        cpu["rel_err_fp64_gpu_vs_oracle"] = float(np.linalg.norm(u.cpu().numpy() - xo) / np.linalg.norm(xo))
+        for name, um in mixed_u.items():
+            mixed[name]["rel_err_vs_fp64_oracle"] = float(np.linalg.norm(um - xo) / np.linalg.norm(xo))
 
     if rank == 0:
         line = dict(
@@ -495,7 +507,7 @@ def run_native(args, world, rank, local):
 
 def run_profile_case(args):
     """One setup + solve of the 2D N=256, T=8 exp-series problem (seeds 1, 2, 3; factors
-    ~0.23 GB, above L2): the small case the ncu captures in profiles/ use."""
+    ~0.23 GB, above L2): a small case for ncu captures of the sweep, ILU(0) and tensor-core kernels."""
     import torch
     from paper_2004_13961_gb300 import lsg
     from paper_2004_13961_gb300 import workloads as W

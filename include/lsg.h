@@ -210,6 +210,17 @@ long long lsg_query(lsg_ctx *ctx, int item);
 /* Free a context and all its device memory. */
 int lsg_destroy(lsg_ctx *ctx);
 
+/* Budget of the device-side dependency waits in this context's triangular sweeps
+ * (Algorithms 3 and 4), in SM clock cycles; 0 restores the default (8e9 cycles,
+ * about 4 s).  The paper has no counterpart: a sweep CTA that waits longer than
+ * this for a value another CTA produces gives up, records LSG_ERR_TIMEOUT in the
+ * context's device error word (reported by the synchronising calls, e.g.
+ * lsg_pcg_solve) and exits after its own bulk copies have landed.  Every compute
+ * call starts with a clear error word, so the context stays usable afterwards.
+ * A budget of a few thousand cycles makes the waits expire on purpose, which is
+ * how the failure path is tested.  cycles < 0: LSG_ERR_ARG. */
+int lsg_set_wait_budget(lsg_ctx *ctx, long long cycles);
+
 /* Batched PCG over `count` independent contexts (uneven sizes allowed):
  * the iterations of all problems are interleaved on the device, each problem
  * stopping at its own tolerance.  F[i], u[i] as in lsg_pcg_solve; infos may

@@ -61,6 +61,16 @@ int read_dev_error(lsg_ctx *c, cudaStream_t s)
     }
 }
 
+// A compute call starts with a clear device error word, so that a context stays
+// usable after a call that reported a timeout; an ILU(0) breakdown found at
+// setup stays recorded (the factors are not valid).
+int clear_dev_error(lsg_ctx *c, cudaStream_t s)
+{
+    if (c->setup_status != LSG_OK) return LSG_OK;
+    LSG_CK(cudaMemsetAsync(c->err, 0, sizeof(int), s));
+    return LSG_OK;
+}
+
 struct Sizes {
     size_t tab, grid, series, band, Lv, Uv, Mkeep, ws, vec, lines;
 };
@@ -247,6 +257,7 @@ int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, con
     c->g = make_geom(d, N, T, Q);
     c->precision = precision;
     c->flags = flags;
+    c->wait_budget = kSpinBudgetCycles;
     if (flags & LSG_SETUP_PROFILE) prof_create(c);
     LSG_CK(cudaGetDevice(&c->device));
     {
@@ -354,6 +365,7 @@ int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, con
     sa = sb = nullptr;
     derr = read_dev_error(c, s);
     if (derr == LSG_ERR_TIMEOUT || derr == LSG_ERR_CUDA) return fail(derr);
+    c->setup_status = derr;
     *out = c;
     return derr;  // LSG_OK or LSG_ERR_ILU_BREAKDOWN (context kept for inspection)
 }
@@ -377,6 +389,7 @@ int lsg_load_vector(lsg_ctx *c, const double *f, double *F, lsg_stream_t stream)
     if (!c || !f || !F) return LSG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const double *df;
+    LSG_TRY(clear_dev_error(c, s));
     LSG_TRY(stage_in(f, c->g.nq, c->fs, &df, s));
     bool hF = !is_device_ptr(F);
     double *dF = hF ? c->ys : F;
@@ -392,6 +405,7 @@ int lsg_apply_A_lowp(lsg_ctx *c, const float *x, float *y, lsg_stream_t stream)
 {
     if (!c || !x || !y || x == y || c->precision == LSG_FP64) return LSG_ERR_ARG;
     if (!is_device_ptr(x) || !is_device_ptr(y)) return LSG_ERR_ARG;
+    LSG_TRY(clear_dev_error(c, (cudaStream_t)stream));
     LSG_TRY(apply_K_tc(c, x, y, nullptr, (cudaStream_t)stream));
     return read_dev_error(c, (cudaStream_t)stream);
 }
@@ -401,6 +415,7 @@ int lsg_apply_A(lsg_ctx *c, const double *x, double *y, lsg_stream_t stream)
     if (!c || !x || !y || x == y) return LSG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const double *dx;
+    LSG_TRY(clear_dev_error(c, s));
     LSG_TRY(stage_in(x, c->g.n, c->xs, &dx, s));
     bool hy = !is_device_ptr(y);
     double *dy = hy ? c->ys : y;
@@ -417,6 +432,7 @@ int lsg_apply_Minv(lsg_ctx *c, const double *r, double *z, lsg_stream_t stream)
     if (!c || !r || !z || r == z) return LSG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const double *dr;
+    LSG_TRY(clear_dev_error(c, s));
     LSG_TRY(stage_in(r, c->g.n, c->xs, &dr, s));
     bool hz = !is_device_ptr(z);
     double *dz = hz ? c->wv : z;
@@ -435,6 +451,7 @@ int lsg_pcg_solve(lsg_ctx *c, const double *F, double *u, double rtol, int kmax,
     if (!c || !F || !u || !(rtol >= 0.0) || kmax < 0) return LSG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const double *dF;
+    LSG_TRY(clear_dev_error(c, s));
     LSG_TRY(stage_in(F, c->g.n, c->fs, &dF, s));
     bool hu = !is_device_ptr(u);
     double *du = u;
@@ -461,6 +478,7 @@ int lsg_eval(lsg_ctx *c, const double *u, double *vals, lsg_stream_t stream)
     if (!c || !u || !vals) return LSG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const double *du;
+    LSG_TRY(clear_dev_error(c, s));
     LSG_TRY(stage_in(u, c->g.n, c->xs, &du, s));
     bool hv = !is_device_ptr(vals);
     double *dv = hv ? c->fs : vals;
@@ -551,6 +569,13 @@ long long lsg_query(lsg_ctx *c, int item)
     case LSG_Q_KX_LO_CALLS: return prof_query(c, PROF_KX_LO, true);
     default: return -1;
     }
+}
+
+int lsg_set_wait_budget(lsg_ctx *c, long long cycles)
+{
+    if (!c || cycles < 0) return LSG_ERR_ARG;
+    c->wait_budget = cycles == 0 ? kSpinBudgetCycles : cycles;
+    return LSG_OK;
 }
 
 }  // extern "C"

@@ -109,6 +109,10 @@ struct lsg_ctx {
     float *r32, *z32, *p32, *w32, *e32, *y32;
     double *e64, *u64;
 
+    // budget (SM clock cycles) of the triangular sweeps' dependency waits (lsg_set_wait_budget)
+    long long wait_budget;
+    int setup_status;          // LSG_OK, or LSG_ERR_ILU_BREAKDOWN (kept in the device error word)
+
     // setup stage times (milliseconds, CUDA events): tables, assembly, ILU(0)
     float t_tables_ms, t_assemble_ms, t_ilu_ms;
     lsg::Prof *prof;           // solve-stage event timing (null unless LSG_SETUP_PROFILE)
@@ -134,12 +138,23 @@ int apply_Minv32(lsg_ctx *c, const float *r, float *z, const int *done, cudaStre
 int pcg_fp64(lsg_ctx *c, const double *F, double *u, double rtol, int kmax, lsg_info *info,
              cudaStream_t s);
 
+// How many iterations to queue before the host looks at the device state again:
+// from the residual decrease observed so far, just enough to reach the stop test,
+// so that few iterations are launched after convergence (they would return at once).
+struct ChunkPlan {
+    double rr0 = 0.0, rr_prev = 0.0;
+    int k_prev = 0;
+};
+int next_chunk(ChunkPlan &P, int k, double rr, double target, int cap);
+
 // non-blocking PCG run (Algorithm 1) used by the batched and serving forms
 struct PcgRun {
     lsg_ctx *c;
     const double *F;
     double *x;
     int kmax, launched, chunk, phase, status;
+    int tag0;                  // profiler tag of the run's first iteration
+    ChunkPlan plan;
     cudaEvent_t ev;
 };
 int pcg_start(PcgRun &R, lsg_ctx *c, const double *F, double *x, double rtol, int kmax, cudaStream_t s);
@@ -149,6 +164,7 @@ void pcg_release(PcgRun &R);
 int pcg_mixed(lsg_ctx *c, const double *F, double *u, double rtol, int kmax, lsg_info *info,
               cudaStream_t s);
 int read_dev_error(lsg_ctx *c, cudaStream_t s);
+int clear_dev_error(lsg_ctx *c, cudaStream_t s);
 int check_finite(lsg_ctx *c, const double *v, long long n, cudaStream_t s);
 size_t workspace_elems(const Geom &g);
 int gauss_rule(int Q, double *x, double *w, cudaStream_t s);
@@ -164,6 +180,12 @@ void prof_reset(lsg_ctx *c);
 int prof_begin(lsg_ctx *c, int stage, cudaStream_t s, int *slot);
 int prof_end(lsg_ctx *c, int slot, cudaStream_t s);
 int prof_collect(lsg_ctx *c);
+// iteration tags: records made while tag q is set count only once prof_mark_done
+// has marked q as an iteration that did its work (kernels of iterations queued
+// after the stop test return at once and are not timed)
+int prof_tag(lsg_ctx *c);
+void prof_set_tag(lsg_ctx *c, int tag);
+void prof_mark_done(lsg_ctx *c, int first_tag, int count);
 long long prof_query(const lsg_ctx *c, int stage, bool calls);
 
 // ---------------------------------------------------------------------------

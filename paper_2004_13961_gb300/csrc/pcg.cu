@@ -5,7 +5,9 @@
 // a last-block combine in block order, so results are bitwise reproducible.
 // The stop test of Algorithm 1 is evaluated on the device and written to a
 // `done` word; every kernel of later iterations returns at once when it is
-// set, so the host only polls the state every few iterations.
+// set.  The host queues iterations in chunks sized from the residual decrease
+// seen so far (next_chunk), so it looks at the device state only a few times
+// per solve and queues few iterations past the stop.
 #include <math.h>
 
 #include <algorithm>
@@ -194,6 +196,29 @@ __global__ void __launch_bounds__(kRedThreads) k_true(long long n, const double 
     }
 }
 
+int next_chunk(ChunkPlan &P, int k, double rr, double target, int cap)
+{
+    // per-iteration factor of r^T r over the whole run and over the last chunk; the
+    // faster of the two (PCG tends to speed up), so that the plan rarely overshoots
+    int m = 2;
+    if (k > 0 && rr > 0.0 && P.rr0 > 0.0 && target > 0.0) {
+        double rate = pow(rr / P.rr0, 1.0 / k);
+        if (k > P.k_prev && P.rr_prev > 0.0) {
+            const double last = pow(rr / P.rr_prev, 1.0 / (k - P.k_prev));
+            if (last < rate) rate = last;
+        }
+        if (rate > 0.0 && rate < 1.0) {
+            const double est = ceil(log(target / rr) / log(rate));
+            m = est < 1.0 ? 1 : (est > cap ? cap : (int)est);
+        } else {
+            m = 4;  // no decrease seen yet
+        }
+    }
+    P.rr_prev = rr;
+    P.k_prev = k;
+    return m < cap ? m : cap;
+}
+
 static int iteration(lsg_ctx *c, double *x, cudaStream_t s)
 {
     const long long n = c->g.n;
@@ -235,6 +260,8 @@ int pcg_start(PcgRun &R, lsg_ctx *c, const double *F, double *x, double rtol, in
     R.kmax = kmax;
     R.launched = 0;
     R.chunk = 2;
+    R.tag0 = -1;
+    R.plan = ChunkPlan{};
     R.phase = 0;
     R.status = LSG_OK;
     if (!R.ev) LSG_CK(cudaEventCreateWithFlags(&R.ev, cudaEventDisableTiming));
@@ -245,6 +272,7 @@ int pcg_start(PcgRun &R, lsg_ctx *c, const double *F, double *x, double rtol, in
     h->kmax = kmax;
     LSG_CK(cudaMemcpyAsync(c->st, h, sizeof(PcgState), cudaMemcpyHostToDevice, s));
     LSG_CK(cudaMemsetAsync(c->counters + 4, 0, sizeof(unsigned), s));
+    LSG_TRY(clear_dev_error(c, s));
     LSG_TRY(apply_K(c, x, c->wv, nullptr, s));
     ::lsg::count_launch();
     k_init<<<kRedBlocks, kRedThreads, 0, s>>>(n, F, c->wv, c->r, c->red, c->counters + 4, c->st);
@@ -283,6 +311,7 @@ int pcg_poll(PcgRun &R, cudaStream_t s, bool wait, bool *finished)
     PcgState *h = c->st_host;
     int derr = dev_err_status(h->pad[0]);
     if (R.phase == 1 || derr == LSG_ERR_TIMEOUT) {
+        if (R.tag0 >= 0) prof_mark_done(c, R.tag0, h->k);
         R.status = h->status;
         if (R.status == LSG_OK && !(h->rr <= h->eps2 * h->nF2)) R.status = LSG_ERR_NOT_CONVERGED;
         if (derr != LSG_OK) R.status = derr;
@@ -299,10 +328,16 @@ int pcg_poll(PcgRun &R, cudaStream_t s, bool wait, bool *finished)
         R.phase = 1;
         return snapshot(R, s);
     }
-    int m = std::min(R.chunk, R.kmax - R.launched);
-    for (int it = 0; it < m; ++it) LSG_TRY(iteration(c, R.x, s));
+    if (R.launched == 0) R.plan.rr0 = h->rr;
+    int m = std::min(next_chunk(R.plan, h->k, h->rr, h->eps2 * h->nF2, 32), R.kmax - R.launched);
+    for (int it = 0; it < m; ++it) {
+        const int tag = prof_tag(c);
+        if (R.tag0 < 0) R.tag0 = tag;
+        prof_set_tag(c, tag);
+        LSG_TRY(iteration(c, R.x, s));
+    }
+    prof_set_tag(c, -1);
     R.launched += m;
-    R.chunk = std::min(R.chunk * 2, 32);
     return snapshot(R, s);
 }
 
@@ -540,18 +575,26 @@ int pcg_mixed(lsg_ctx *c, const double *F, double *u, double rtol, int kmax, lsg
         ::lsg::count_launch();
         k_init32<<<kRedBlocks, kRedThreads, 0, s>>>(n, c->r32, c->red, c->counters + 4, c->st);
         LSG_CK(cudaGetLastError());
-        int chunk = 4, launched = 0;
+        int launched = 0, tag0 = -1;
+        ChunkPlan plan;
         for (;;) {
             LSG_CK(cudaMemcpyAsync(h, c->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
             LSG_CK(cudaStreamSynchronize(s));
             if (h->done || launched >= kmax - total) break;
             int e = read_dev_error(c, s);
             if (e != LSG_OK) return e;
-            int m = std::min(chunk, kmax - total - launched);
-            for (int it = 0; it < m; ++it) LSG_TRY(iteration32(c, s));
+            if (launched == 0) plan.rr0 = h->rr;
+            int m = std::min(next_chunk(plan, h->k, h->rr, h->eps2 * h->nF2, 32), kmax - total - launched);
+            for (int it = 0; it < m; ++it) {
+                const int tag = prof_tag(c);
+                if (tag0 < 0) tag0 = tag;
+                prof_set_tag(c, tag);
+                LSG_TRY(iteration32(c, s));
+            }
+            prof_set_tag(c, -1);
             launched += m;
-            chunk = std::min(chunk * 2, 32);
         }
+        if (tag0 >= 0) prof_mark_done(c, tag0, h->k);
         total += h->k;
         last_inner = h->nF2 > 0 ? sqrt(h->rr / h->nF2) : 0.0;
         int e = read_dev_error(c, s);

@@ -76,7 +76,8 @@ __device__ __forceinline__ bool wait_flag(const unsigned *flag, unsigned need, i
 // Like wait_flag, but remembers the last value seen in *seen, so that a caller
 // that polls the same word row after row only goes to memory when the cached
 // value is not enough.
-__device__ __forceinline__ bool wait_flag_cached(const unsigned *flag, unsigned need, int *err, unsigned *seen)
+__device__ __forceinline__ bool wait_flag_cached(const unsigned *flag, unsigned need, int *err, unsigned *seen,
+                                                 long long budget)
 {
     if (*seen >= need) return true;
     long long t0 = 0;
@@ -88,7 +89,7 @@ __device__ __forceinline__ bool wait_flag_cached(const unsigned *flag, unsigned 
         }
         if (it == 0) t0 = clock64();
         if ((it & 15) == 15 && *(volatile int *)err != 0) return false;
-        if (clock64() - t0 > kSpinBudgetCycles) {
+        if (clock64() - t0 > budget) {
             set_err(err, DERR_TIMEOUT);
             return false;
         }

@@ -60,6 +60,7 @@ struct SweepArgs {
     int *err;
     int B;               // lines per CTA (k_sweep)
     int K;               // fresh window (k_sweep_line)
+    long long budget;    // SM clock cycles a dependency wait may take before it reports a timeout
 };
 
 // ---- asynchronous copy and mbarrier primitives (inline PTX, sm_90+) --------
@@ -110,30 +111,15 @@ __device__ __forceinline__ void prefetch_l2(const void *gsrc, unsigned bytes)
 }
 
 // Bounded wait for an mbarrier phase (every lane polls, so each gets acquire order).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int *err)
+// Waits for copies this CTA issued itself (before it exits) keep the default budget.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int *err,
+                                          long long budget = kSpinBudgetCycles)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > kSpinBudgetCycles) {
-            set_err(err, DERR_TIMEOUT);
-            return false;
-        }
-    }
-}
-
-// Bounded spin until a shared word reaches `need` (sleeping between polls).
-__device__ __forceinline__ bool wait_smem_at_least(const unsigned *w, unsigned need, const volatile int *abort_flag,
-                                                   int *err)
-{
-    if (*(volatile const unsigned *)w >= need) return true;
-    const long long t0 = clock64();
-    for (;;) {
-        __nanosleep(20);
-        if (*(volatile const unsigned *)w >= need) return true;
-        if (*abort_flag) return false;
-        if (clock64() - t0 > kSpinBudgetCycles) {
+        if (clock64() - t0 > budget) {
             set_err(err, DERR_TIMEOUT);
             return false;
         }
@@ -180,7 +166,8 @@ __device__ __forceinline__ void st_release_cta(volatile int *p, int v)
 
 // Bounded spin until a shared counter reaches `need`: tight polls first (the
 // producer is a warp of this CTA a few hundred cycles away), then sleeps.
-__device__ __forceinline__ bool wait_count(const volatile int *c, int need, const volatile int *abort_flag, int *err)
+__device__ __forceinline__ bool wait_count(const volatile int *c, int need, const volatile int *abort_flag, int *err,
+                                           long long budget)
 {
     if (*c >= need) return true;
     const long long t0 = clock64();
@@ -189,7 +176,7 @@ __device__ __forceinline__ bool wait_count(const volatile int *c, int need, cons
         if (it >= 64) __nanosleep(32);
         if ((it & 15) == 15) {
             if (*abort_flag) return false;
-            if (clock64() - t0 > kSpinBudgetCycles) {
+            if (clock64() - t0 > budget) {
                 set_err(err, DERR_TIMEOUT);
                 return false;
             }
@@ -317,7 +304,7 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
                     if (all) break;
                     if (!any) {
                         if (it > 64) __nanosleep(32);
-                        if (clock64() - t0 > 4 * kSpinBudgetCycles) {
+                        if (clock64() - t0 > 4 * A.budget) {
                             set_err(A.err, DERR_TIMEOUT);
                             break;
                         }
@@ -377,7 +364,7 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
                 if (it > 32) __nanosleep(32);
                 // warp-uniform exits (the loop uses full-warp collectives)
                 if (__any_sync(0xffffffffu, s_abort != 0)) break;
-                if (__any_sync(0xffffffffu, clock64() - t0 > 4 * kSpinBudgetCycles)) {
+                if (__any_sync(0xffffffffu, clock64() - t0 > 4 * A.budget)) {
                     if (lane == 0) set_err(A.err, DERR_TIMEOUT);
                     break;
                 }
@@ -413,7 +400,7 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
                     if (moved && pub == n1) finished = true;
                 } else {
                     if (it > 64) __nanosleep(32);
-                    if (clock64() - t0 > 4 * kSpinBudgetCycles) {  // the compute warps' waits are bounded
+                    if (clock64() - t0 > 4 * A.budget) {  // the compute warps' waits are bounded
                         set_err(A.err, DERR_TIMEOUT);
                         finished = true;
                     }
@@ -472,10 +459,10 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
                 bool fast = ld_acquire_cta(prevc) >= need && (b != 0 || ld_acquire_cta(&s_far) >= needfar);
                 if (vplane >= 0) fast = fast && seen_plane >= (unsigned)needfar;
                 if (__all_sync(0xffffffffu, fast)) return true;
-                bool good = wait_count(prevc, need, &s_abort, A.err);
-                if (good && b == 0) good = wait_count(&s_far, needfar, &s_abort, A.err);
+                bool good = wait_count(prevc, need, &s_abort, A.err, A.budget);
+                if (good && b == 0) good = wait_count(&s_far, needfar, &s_abort, A.err, A.budget);
                 if (good && vplane >= 0)
-                    good = wait_flag_cached(A.gprog + plane_real, (unsigned)needfar, A.err, &seen_plane);
+                    good = wait_flag_cached(A.gprog + plane_real, (unsigned)needfar, A.err, &seen_plane, A.budget);
                 good = __all_sync(0xffffffffu, good);
                 __threadfence_block();
                 return good;
@@ -547,7 +534,7 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
             };
             auto wait_row = [&](int q) -> bool {
                 const int slot = q % SW_D;
-                bool good = mbar_wait(&mybar[slot], (phase >> slot) & 1u, A.err);
+                bool good = mbar_wait(&mybar[slot], (phase >> slot) & 1u, A.err, A.budget);
                 phase ^= 1u << slot;
                 ++waited;
                 return __all_sync(0xffffffffu, good);
@@ -762,7 +749,8 @@ __host__ __device__ inline LineSmem line_layout(int d, int n1, int w, int D, int
 
 // Bounded spin until a shared counter reaches `need`; every lane polls with
 // acquire loads and the result is warp-uniform.
-__device__ __forceinline__ bool wait_ge(const volatile int *c, int need, const volatile int *abort_flag, int *err)
+__device__ __forceinline__ bool wait_ge(const volatile int *c, int need, const volatile int *abort_flag, int *err,
+                                        long long budget)
 {
     bool good = true;
     if (ld_acquire_cta(c) < need) {
@@ -775,7 +763,7 @@ __device__ __forceinline__ bool wait_ge(const volatile int *c, int need, const v
                     good = false;
                     break;
                 }
-                if (clock64() - t0 > kSpinBudgetCycles) {
+                if (clock64() - t0 > budget) {
                     set_err(err, DERR_TIMEOUT);
                     good = false;
                     break;
@@ -790,7 +778,8 @@ __device__ __forceinline__ bool wait_ge(const volatile int *c, int need, const v
 // pattern: the value itself is the flag (all lanes read the same address; the
 // result is warp-uniform).
 template <typename AT>
-__device__ __forceinline__ bool poll_value(const AT *p, AT &val, const volatile int *abort_flag, int *err)
+__device__ __forceinline__ bool poll_value(const AT *p, AT &val, const volatile int *abort_flag, int *err,
+                                           long long budget)
 {
     using bits_t = typename Fill<AT>::bits;
     const volatile bits_t *vp = reinterpret_cast<const volatile bits_t *>(p);
@@ -807,7 +796,7 @@ __device__ __forceinline__ bool poll_value(const AT *p, AT &val, const volatile 
                     good = false;
                     break;
                 }
-                if (clock64() - t0 > kSpinBudgetCycles) {
+                if (clock64() - t0 > budget) {
                     set_err(err, DERR_TIMEOUT);
                     good = false;
                     break;
@@ -822,7 +811,8 @@ __device__ __forceinline__ bool poll_value(const AT *p, AT &val, const volatile 
 // Bounded poll of a value of another CTA's line in global memory (final once it
 // differs from the fill pattern); per lane, no warp collectives.
 template <typename AT>
-__device__ __forceinline__ bool poll_global(const AT *p, AT &val, const volatile int *abort_flag, int *err)
+__device__ __forceinline__ bool poll_global(const AT *p, AT &val, const volatile int *abort_flag, int *err,
+                                            long long budget)
 {
     const long long t0 = clock64();
     for (int it = 0;; ++it) {
@@ -834,7 +824,7 @@ __device__ __forceinline__ bool poll_global(const AT *p, AT &val, const volatile
         __nanosleep(32);
         if ((it & 15) == 15) {
             if (*abort_flag || *(volatile int *)err != 0) return false;
-            if (clock64() - t0 > kSpinBudgetCycles) {
+            if (clock64() - t0 > budget) {
                 set_err(err, DERR_TIMEOUT);
                 return false;
             }
@@ -847,17 +837,19 @@ __device__ __forceinline__ bool poll_global(const AT *p, AT &val, const volatile
 // holds no loop of its own.
 template <typename AT>
 __device__ __noinline__ bool poll_operands(const AT *pT, const AT *pP, AT *Tv, AT *yp, const volatile int *abort_flag,
-                                           int *err)
+                                           int *err, long long budget)
 {
     AT a, b = AT(0);
-    const bool good = poll_value(pT, a, abort_flag, err) && (pP == nullptr || poll_value(pP, b, abort_flag, err));
+    const bool good =
+        poll_value(pT, a, abort_flag, err, budget) && (pP == nullptr || poll_value(pP, b, abort_flag, err, budget));
     *Tv = a;
     if (pP != nullptr) *yp = b;
     return good;
 }
 
 // Bounded wait for an mbarrier phase that also gives up when the CTA aborts.
-__device__ __forceinline__ bool mbar_wait_ab(uint64_t *bar, unsigned parity, const volatile int *abort_flag, int *err)
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t *bar, unsigned parity, const volatile int *abort_flag, int *err,
+                                             long long budget)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
@@ -865,7 +857,7 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t *bar, unsigned parity, con
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 15) == 15) {
             if (*abort_flag) return false;
-            if (clock64() - t0 > kSpinBudgetCycles) {
+            if (clock64() - t0 > budget) {
                 set_err(err, DERR_TIMEOUT);
                 return false;
             }
@@ -940,7 +932,7 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
         return (unsigned)(((it & cnt) ^ (c / NB)) & 1);
     };
     auto wait_chunk = [&](int it, int q) -> bool {
-        return __all_sync(FULL, mbar_wait_ab(&mbar[(q / L1_CH) % NB], parity(it, q), &s_abort, A.err));
+        return __all_sync(FULL, mbar_wait_ab(&mbar[(q / L1_CH) % NB], parity(it, q), &s_abort, A.err, A.budget));
     };
 
     // stale warps: register-resident stencil offsets (row buffers of this CTA) and
@@ -1091,7 +1083,7 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
             if (ok) next_operands(s0);
             for (int s = s0; s < 0 && ok; ++s) {
                 AT yp = FB::val(pb);
-                if (pb == FB::v) ok = poll_value(&sy[prevoff + (DIR > 0 ? s : n1 - 1 - s)], yp, &s_abort, A.err);
+                if (pb == FB::v) ok = poll_value(&sy[prevoff + (DIR > 0 ? s : n1 - 1 - s)], yp, &s_abort, A.err, A.budget);
                 if (!ok) break;
                 const AT r = fma(-fp, yp, Gw);
                 Gw = __shfl_down_sync(FULL, r, 1);
@@ -1106,7 +1098,7 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
                 AT Tv = FB::val(tb), yp = FB::val(pb);
                 if (__any_sync(FULL, tb == FB::v || pb == FB::v)) {
                     if (!poll_operands(&sT[s % L1_DT], G.d >= 2 ? &sy[prevoff + (DIR > 0 ? s : n1 - 1 - s)] : nullptr,
-                                       &Tv, &yp, &s_abort, A.err))
+                                       &Tv, &yp, &s_abort, A.err, A.budget))
                         return false;
                 }
                 Bv = fma(-fp, yp, (j == 0) ? Tv : AT(0));
@@ -1149,10 +1141,10 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
             // positions < q-K and previous-line positions <= q+w-K are final once the
             // finisher has done q-K positions and line v-1 is staged that far
             for (int q = sw; q < n1 && ok; q += L1_NS) {
-                ok = wait_ge(&s_prog, q - K, &s_abort, A.err) &&
-                     wait_ge(&s_near, min(max(0, q + w - K + 1), n1), &s_abort, A.err) &&
-                     wait_ge(&s_near2, min(q + w + 1, n1), &s_abort, A.err) &&
-                     wait_ge(&s_far, min(q + w + 1, n1), &s_abort, A.err) && wait_chunk(it, q);
+                ok = wait_ge(&s_prog, q - K, &s_abort, A.err, A.budget) &&
+                     wait_ge(&s_near, min(max(0, q + w - K + 1), n1), &s_abort, A.err, A.budget) &&
+                     wait_ge(&s_near2, min(q + w + 1, n1), &s_abort, A.err, A.budget) &&
+                     wait_ge(&s_far, min(q + w + 1, n1), &s_abort, A.err, A.budget) && wait_chunk(it, q);
                 if (!ok) break;
                 const int i = DIR > 0 ? q : n1 - 1 - q;
                 const V *row = ring + (size_t)(q % D) * RL + (DIR > 0 ? 0 : 1);
@@ -1195,7 +1187,7 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
 #pragma unroll
                             for (int u = 0; u < G3; ++u)
                                 if (good && (pend >> u & 1u))
-                                    good = poll_global(obase + tab[t0 + 32 * u].x, yv[u], &s_abort, A.err);
+                                    good = poll_global(obase + tab[t0 + 32 * u].x, yv[u], &s_abort, A.err, A.budget);
                             if (!__all_sync(FULL, good)) {
                                 ok = false;
                                 break;
@@ -1266,7 +1258,7 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
                     }
                     if (!any) {
                         if (itp > 64) __nanosleep(32);
-                        if (clock64() - t0 > 4 * kSpinBudgetCycles) {
+                        if (clock64() - t0 > 4 * A.budget) {
                             set_err(A.err, DERR_TIMEOUT);
                             ok = false;
                             break;
@@ -1308,7 +1300,7 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
                     if (itp > 64) __nanosleep(32);
                     if ((itp & 15) == 15) {
                         bool stop = s_abort != 0 || *(volatile int *)A.err != 0;
-                        if (clock64() - t0 > 4 * kSpinBudgetCycles) {
+                        if (clock64() - t0 > 4 * A.budget) {
                             if (lane == 0) set_err(A.err, DERR_TIMEOUT);
                             stop = true;
                         }
@@ -1367,7 +1359,7 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
                     if (itp > 64) __nanosleep(32);
                     if ((itp & 15) == 15) {
                         bool stop = s_abort != 0 || *(volatile int *)A.err != 0;
-                        if (clock64() - t0 > 4 * kSpinBudgetCycles) {
+                        if (clock64() - t0 > 4 * A.budget) {
                             if (lane == 0) set_err(A.err, DERR_TIMEOUT);
                             stop = true;
                         }
@@ -1458,6 +1450,7 @@ static int sweeps_line(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done
     A.G = sgeo(g);
     A.done = done;
     A.err = c->err;
+    A.budget = c->wait_budget;
     A.B = 1;
     // fresh window: the stale part of a row may start K positions before the row
     // is finished, which covers its ~1 us FP64 reduction at a few hundred ns per position;
@@ -1508,6 +1501,7 @@ static int sweeps(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done, cud
     A.G = sgeo(g);
     A.done = done;
     A.err = c->err;
+    A.budget = c->wait_budget;
     // lines per CTA: one per SM sub-partition (an FP64 warp instruction occupies its
     // sub-partition's FP64 unit for ~64 clocks; in FP32 a second line per
     // sub-partition measured slower too); fewer if shared memory runs out

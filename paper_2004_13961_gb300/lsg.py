@@ -39,7 +39,8 @@ SYMBOLS = [
     "lsg_version", "lsg_status_string", "lsg_last_error", "lsg_kernel_launches", "lsg_gauss", "lsg_gauss_noalloc", "lsg_footprint_bytes",
     "lsg_setup", "lsg_setup_ex", "lsg_load_vector", "lsg_apply_A", "lsg_apply_A_lowp", "lsg_apply_Minv",
     "lsg_pcg_solve",
-    "lsg_eval", "lsg_export_count", "lsg_export", "lsg_query", "lsg_destroy", "lsg_batch_solve",
+    "lsg_eval", "lsg_export_count", "lsg_export", "lsg_query", "lsg_destroy", "lsg_set_wait_budget",
+    "lsg_batch_solve",
     "lsg_server_create", "lsg_server_submit", "lsg_server_poll", "lsg_server_drain",
     "lsg_server_release", "lsg_server_destroy",
 ]
@@ -104,6 +105,7 @@ def load(build_if_needed: bool = True):
     L.lsg_query.argtypes = [vp, ci]
     L.lsg_query.restype = cll
     L.lsg_destroy.argtypes = [vp]
+    L.lsg_set_wait_budget.argtypes = [vp, cll]
     L.lsg_batch_solve.argtypes = [ci, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), cd, ci,
                                   ctypes.POINTER(LsgInfo), vp]
     L.lsg_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t, ci]
@@ -279,6 +281,10 @@ class Context:
 
     def query(self, item):
         return int(self._L.lsg_query(self._h, item))
+
+    def set_wait_budget(self, cycles):
+        """Budget (SM clock cycles) of the sweeps' dependency waits; 0 = default."""
+        _check(self._L.lsg_set_wait_budget(self._h, int(cycles)), "lsg_set_wait_budget")
 
 
 def batch_solve(ctxs, Fs, us, rtol=1e-12, kmax=10000, stream=None):

@@ -70,7 +70,7 @@ def test_fp32_ilu_factors_track_fp64_oracle(lsg):
     ctx.close()
 
 
-@pytest.mark.parametrize("case", [(2, 33, 5), (3, 10, 2)])
+@pytest.mark.parametrize("case", [(2, 33, 5), (3, 10, 2), (3, 12, 8)])
 def test_mixed_context_preconditioner_solve(lsg, case):
     """A mixed context's FP32 ILU(0) factors swept with FP64 vectors (lsg_apply_Minv) against
     the oracle's FP64 factors and solve: the factors carry FP32 rounding, so the result agrees
