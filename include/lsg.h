@@ -207,7 +207,11 @@ long long lsg_export_count(lsg_ctx *ctx, int item);
 int lsg_export(lsg_ctx *ctx, int item, double *out);
 /* Integer properties of a context (-1 for an unknown item). */
 long long lsg_query(lsg_ctx *ctx, int item);
-/* Free a context and all its device memory. */
+/* Free a context and all its device memory.  The release is ordered on the
+ * stream of the context's last call (lsg_setup or a compute call) and waits for
+ * that stream only, not for the whole device, so that contexts on other streams
+ * keep running; work the caller queued with this context on other streams must
+ * be complete (or ordered before that stream) when it calls lsg_destroy. */
 int lsg_destroy(lsg_ctx *ctx);
 
 /* Budget of the device-side dependency waits in this context's triangular sweeps
@@ -250,8 +254,15 @@ typedef struct {
 } lsg_result;
 
 /* Create a server with an HBM budget (bytes) for admitted requests and up to
- * max_inflight concurrently running solves (each on its own stream). */
+ * max_inflight concurrently running solves (each on its own stream).  Admission:
+ * among the queued requests whose footprint (lsg_footprint_bytes) fits the free
+ * budget, the smallest first (the earliest on ties), so short solves are not held
+ * behind large ones; but once the oldest queued request has waited longer than
+ * the aging bound (default 2000 ms), it alone may be admitted next, so that large
+ * requests are not starved by a steady stream of small ones. */
 int lsg_server_create(lsg_server **srv, size_t hbm_budget, int max_inflight);
+/* Set the aging bound of a server in milliseconds (> 0). */
+int lsg_server_set_aging(lsg_server *srv, double ms);
 /* Queue a request; returns LSG_ERR_NOMEM if it can never fit the budget. */
 int lsg_server_submit(lsg_server *srv, const lsg_request *req);
 /* Collect up to `max` finished results; *count receives how many. */

@@ -6,6 +6,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
+#include <vector>
 
 #include "lsg_internal.cuh"
 
@@ -66,6 +68,7 @@ int read_dev_error(lsg_ctx *c, cudaStream_t s)
 // setup stays recorded (the factors are not valid).
 int clear_dev_error(lsg_ctx *c, cudaStream_t s)
 {
+    c->stream = s;  // the stream lsg_destroy orders the release after
     if (c->setup_status != LSG_OK) return LSG_OK;
     LSG_CK(cudaMemsetAsync(c->err, 0, sizeof(int), s));
     return LSG_OK;
@@ -152,7 +155,44 @@ static int check_sizes(int d, int N, int T, int Q)
     return LSG_OK;
 }
 
-static void free_ctx(lsg_ctx *c)
+// Pinned host mirrors of the PCG state, reused across contexts: cudaMallocHost and
+// cudaFreeHost are slow and may synchronise the device, which would serialise the
+// contexts that a server sets up and tears down while others compute.
+static std::mutex g_pin_mu;
+static std::vector<PcgState *> g_pin_free;
+
+static PcgState *pinned_state()
+{
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        if (!g_pin_free.empty()) {
+            PcgState *p = g_pin_free.back();
+            g_pin_free.pop_back();
+            return p;
+        }
+    }
+    // one allocation for a slab of states, handed out one by one
+    constexpr int kSlab = 64;
+    PcgState *slab = nullptr;
+    if (cudaMallocHost((void **)&slab, sizeof(PcgState) * kSlab) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    for (int i = 1; i < kSlab; ++i) g_pin_free.push_back(slab + i);
+    return slab;
+}
+
+static void release_pinned_state(PcgState *p)
+{
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(p);
+}
+
+// Frees a context's device memory in the order of stream `s` (no device-wide
+// synchronisation), waits for that stream only, then returns the pinned state.
+static void free_ctx(lsg_ctx *c, cudaStream_t s)
 {
     if (!c) return;
     void *ptrs[] = {c->gx, c->gw, c->tab, c->Wa, c->Wb, c->Wg, c->ahat, c->bhat, c->bandS, c->bandM,
@@ -160,8 +200,10 @@ static void free_ctx(lsg_ctx *c)
                     c->r, c->z, c->p, c->wv, c->xs, c->fs, c->ys, c->red, c->st, c->r32, c->z32, c->p32, c->w32,
                     c->e32, c->e64, c->u64, c->y32, c->Wa32, c->Wb32, c->tct};
     for (void *p : ptrs)
-        if (p) cudaFree(p);
-    if (c->st_host) cudaFreeHost(c->st_host);
+        if (p) cudaFreeAsync(p, s);
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    release_pinned_state(c->st_host);
     prof_destroy(c);
     delete c;
 }
@@ -254,6 +296,7 @@ int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, con
     if (precision < LSG_FP64 || precision > LSG_MIXED_BF16) return LSG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     lsg_ctx *c = new lsg_ctx{};
+    c->stream = s;
     c->g = make_geom(d, N, T, Q);
     c->precision = precision;
     c->flags = flags;
@@ -323,15 +366,11 @@ int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, con
     if (ha) ALLOC(sa, z.grid);
     if (hb) ALLOC(sb, z.grid);
 #undef ALLOC
-    if (st == LSG_OK && cudaMallocHost((void **)&c->st_host, sizeof(PcgState)) != cudaSuccess) {
-        cudaGetLastError();
-        st = LSG_ERR_NOMEM;
-    }
+    if (st == LSG_OK && !(c->st_host = pinned_state())) st = LSG_ERR_NOMEM;
     if (st != LSG_OK) {
         if (sa) cudaFreeAsync(sa, s);
         if (sb) cudaFreeAsync(sb, s);
-        cudaStreamSynchronize(s);
-        free_ctx(c);
+        free_ctx(c, s);
         return st;
     }
     c->bytes += 0;
@@ -339,8 +378,7 @@ int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, con
     auto fail = [&](int code) {
         if (sa) cudaFreeAsync(sa, s);
         if (sb) cudaFreeAsync(sb, s);
-        cudaStreamSynchronize(s);
-        free_ctx(c);
+        free_ctx(c, s);
         return code;
     };
     if (ha) {
@@ -379,8 +417,7 @@ int lsg_setup(lsg_ctx **out, int d, int N, int T, int Q, const double *a, const 
 int lsg_destroy(lsg_ctx *c)
 {
     if (!c) return LSG_ERR_ARG;
-    cudaDeviceSynchronize();
-    free_ctx(c);
+    free_ctx(c, c->stream);
     return LSG_OK;
 }
 

@@ -111,6 +111,7 @@ struct lsg_ctx {
 
     // budget (SM clock cycles) of the triangular sweeps' dependency waits (lsg_set_wait_budget)
     long long wait_budget;
+    cudaStream_t stream;       // stream of the last call (setup or compute): lsg_destroy frees on it
     int setup_status;          // LSG_OK, or LSG_ERR_ILU_BREAKDOWN (kept in the device error word)
 
     // setup stage times (milliseconds, CUDA events): tables, assembly, ILU(0)

@@ -41,7 +41,7 @@ SYMBOLS = [
     "lsg_pcg_solve",
     "lsg_eval", "lsg_export_count", "lsg_export", "lsg_query", "lsg_destroy", "lsg_set_wait_budget",
     "lsg_batch_solve",
-    "lsg_server_create", "lsg_server_submit", "lsg_server_poll", "lsg_server_drain",
+    "lsg_server_create", "lsg_server_set_aging", "lsg_server_submit", "lsg_server_poll", "lsg_server_drain",
     "lsg_server_release", "lsg_server_destroy",
 ]
 
@@ -109,6 +109,7 @@ def load(build_if_needed: bool = True):
     L.lsg_batch_solve.argtypes = [ci, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), cd, ci,
                                   ctypes.POINTER(LsgInfo), vp]
     L.lsg_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t, ci]
+    L.lsg_server_set_aging.argtypes = [vp, cd]
     L.lsg_server_submit.argtypes = [vp, ctypes.POINTER(LsgRequest)]
     L.lsg_server_poll.argtypes = [vp, ctypes.POINTER(LsgResult), ci, ctypes.POINTER(ci)]
     L.lsg_server_drain.argtypes = [vp]
@@ -302,12 +303,14 @@ class Server:
     """Continuous batching of solve requests (lsg_server_*): requests are admitted as
     worker slots and HBM budget free up, and run on their own streams."""
 
-    def __init__(self, hbm_budget, max_inflight=4):
+    def __init__(self, hbm_budget, max_inflight=4, aging_ms=None):
         L = load()
         self._L = L
         h = ctypes.c_void_p(0)
         _check(L.lsg_server_create(ctypes.byref(h), int(hbm_budget), int(max_inflight)), "lsg_server_create")
         self._h = h
+        if aging_ms is not None:
+            _check(L.lsg_server_set_aging(h, float(aging_ms)), "lsg_server_set_aging")
 
     def submit(self, rid, d, N, T, a, b, f, Q=None, precision=FP64, rtol=1e-10, kmax=10000):
         """Queue one request; a, b, f are host float64 arrays of Q^d samples (copied)."""

@@ -182,6 +182,36 @@ def test_ilu0_factors(lsg, case):
     ctx.close()
 
 
+def _breakdown_agreement(lsg, ctx, ref, d, N, T):
+    """The device eliminates rows in wavefront-level order (reading C19) and stops claiming rows
+    once a pivot fails; the oracle (Algorithm 2, natural order) goes on to the end.  Compared in
+    level order: every pivot the device finished up to the oracle's first failing level equals the
+    oracle's, no row fails on the device before that level, and the device does fail."""
+    n1, w = N - 1, T + 2
+    n = ref["LU"].n
+    piv = np.array([ref["LU"].get(i, i) for i in range(n)])
+    mii = np.array([ref["M"].get(i, i) for i in range(n)])
+    r = np.arange(n)
+    level = r % n1 + (w + 1) * ((r // n1) % n1) + (w + 1) ** 2 * (r // (n1 * n1))
+    if d == 1:
+        level = r
+    bad = piv <= 1e-14 * np.abs(mii)
+    Lb = level[bad].min()
+    assert ctx.status == lsg.ERR_ILU_BREAKDOWN
+    st = ctx.export(lsg.EXPORT_LU).reshape(n, -1)
+    Sc = (st.shape[1] - 1) // 2
+    gm = ctx.export(lsg.EXPORT_M).reshape(n, -1)[:, Sc]
+    assert rel_max(gm, mii) < 1e-13
+    gp = st[:, Sc]
+    done = gp != gm  # rows the device finished (the others still hold M's assembled diagonal)
+    upto = done & (level <= Lb)
+    assert upto.sum() > 0
+    assert np.abs(gp[upto] - piv[upto]).max() < 1e-10 * np.abs(piv[upto]).max()
+    gbad = done & (gp <= 1e-14 * np.abs(gm))
+    assert gbad.any() and level[gbad].min() >= Lb
+    assert np.all(gp[done & (level < Lb)] > 0)
+
+
 def test_ilu0_breakdown_agrees_with_oracle(lsg):
     """3D, T=1: the truncated series is too coarse and ILU(0) meets a negative pivot;
     the oracle (Algorithm 2) and the device report the same breakdown."""
@@ -189,40 +219,24 @@ def test_ilu0_breakdown_agrees_with_oracle(lsg):
     p = problem(d, N, T, 1, True, seed=17)
     ref = O.setup(d, N, p["Q"], T, p["a"], p["b"])
     assert ref["ilu_status"] == O.OR_ERR_BREAKDOWN
-    ctx = lsg.Context(d, N, T, cuda(p["a"]), cuda(p["b"]), Q=p["Q"], allow_breakdown=True)
-    assert ctx.status == lsg.ERR_ILU_BREAKDOWN
-    # the factors up to and including the first bad pivot agree
-    st = ctx.export(lsg.EXPORT_LU).reshape(ref["LU"].n, -1)
-    Sc = (st.shape[1] - 1) // 2
-    piv = np.diag(ref["LU"].to_dense())
-    first = int(np.argmax(piv <= 0))
-    assert np.abs(st[: first + 1, Sc] - piv[: first + 1]).max() < 1e-10 * np.abs(piv).max()
+    ctx = lsg.Context(d, N, T, cuda(p["a"]), cuda(p["b"]), Q=p["Q"], allow_breakdown=True, keep_M=True)
+    _breakdown_agreement(lsg, ctx, ref, d, N, T)
     ctx.close()
 
 
 def test_ilu0_breakdown_2d_serving_contrast(lsg):
     """2D, T=4, N=64 with the serving mix's largest contrast (sigma = 2.3, a up to ~100):
-    the truncated series of degree 4 no longer keeps M's ILU(0) pivots positive.  The
-    oracle (Algorithm 2) and the device meet the first non-positive pivot at the same row,
-    and every pivot before it agrees."""
+    the truncated series of degree 4 no longer keeps M's ILU(0) pivots positive.  The first
+    failing row is 167 in natural order, but row 194 (wavefront level 26) in level order."""
     d, N, T = 2, 64, 4
     p = W.random_exp_problem(d, N, T, 100000, 100001, 100002, sigma=2.3)
     ref = O.setup(d, N, p["Q"], T, p["a"], p["b"])
     assert ref["ilu_status"] == O.OR_ERR_BREAKDOWN
-    n = ref["LU"].n
-    piv = np.array([ref["LU"].get(i, i) for i in range(n)])
-    mii = np.array([ref["M"].get(i, i) for i in range(n)])
-    first = int(np.argmax(piv <= 1e-14 * np.abs(mii)))
-    assert first == 167  # the oracle's first bad row for this seed (natural order)
+    piv = np.array([ref["LU"].get(i, i) for i in range(ref["LU"].n)])
+    mii = np.array([ref["M"].get(i, i) for i in range(ref["LU"].n)])
+    assert int(np.argmax(piv <= 1e-14 * np.abs(mii))) == 167
     ctx = lsg.Context(d, N, T, cuda(p["a"]), cuda(p["b"]), Q=p["Q"], allow_breakdown=True, keep_M=True)
-    assert ctx.status == lsg.ERR_ILU_BREAKDOWN
-    st = ctx.export(lsg.EXPORT_LU).reshape(n, -1)
-    Sc = (st.shape[1] - 1) // 2
-    gm = ctx.export(lsg.EXPORT_M).reshape(n, -1)[:, Sc]
-    assert rel_max(gm, mii) < 1e-13
-    gfirst = int(np.argmax(st[:, Sc] <= 1e-14 * np.abs(gm)))
-    assert gfirst == first
-    assert np.abs(st[: first + 1, Sc] - piv[: first + 1]).max() < 1e-10 * np.abs(piv[: first + 1]).max()
+    _breakdown_agreement(lsg, ctx, ref, d, N, T)
     ctx.close()
 
 
