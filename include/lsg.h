@@ -72,6 +72,9 @@ enum lsg_precision {
                                 lsg_pcg_solve launches, with CUDA events recorded on the solve's
                                 stream (no extra synchronisation); read with the LSG_Q_SWEEP_* and
                                 LSG_Q_KX_* queries after the solve returns */
+#define LSG_SETUP_AUTOTUNE 4u /* when the committed tile table has no entry for (d, N, Q), time the
+                                 tile variants of the FP64 contractions of K x at setup and keep
+                                 the fastest (lsg_autotune_transforms) */
 
 /* lsg_export items (host output; sizes from lsg_export_count) */
 enum lsg_export_item {
@@ -213,6 +216,23 @@ long long lsg_query(lsg_ctx *ctx, int item);
  * keep running; work the caller queued with this context on other streams must
  * be complete (or ordered before that stream) when it calls lsg_destroy. */
 int lsg_destroy(lsg_ctx *ctx);
+
+/* Autotuner of the FP64 K x transforms (Sec. 4.3 steps 2-3 as dense contractions,
+ * one per direction forward and one backward).  Each contraction has five tile
+ * shapes (output rows x batch columns per CTA: 16x16, 16x32, 32x32, 32x64, 64x32,
+ * numbered 0-4); for each contraction in turn this times K x with every shape on
+ * the context's last stream (the others at their current choice), keeps the
+ * fastest, and sweeps twice.  The choice is kept by the context and, for later
+ * contexts of the same (d, N, Q), by the process.  Contexts whose size is in the
+ * library's committed table (tuned on a GB300) start with that choice.
+ * choice (may be NULL): 6 ints, forward contractions 1..3 then backward 1..3
+ * (-1: the default shape; entries past d unused).  reps: timed K x per variant
+ * (< 1: 5).  Synchronises. */
+int lsg_autotune_transforms(lsg_ctx *ctx, int reps, int *choice);
+/* The tile choice a context uses (6 ints, as lsg_autotune_transforms). */
+int lsg_transform_tiles(lsg_ctx *ctx, int *choice);
+/* Set the tile choice of a context (6 ints in -1..4, as lsg_autotune_transforms). */
+int lsg_set_transform_tiles(lsg_ctx *ctx, const int *choice);
 
 /* Budget of the device-side dependency waits in this context's triangular sweeps
  * (Algorithms 3 and 4), in SM clock cycles; 0 restores the default (8e9 cycles,

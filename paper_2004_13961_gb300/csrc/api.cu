@@ -17,6 +17,8 @@ static thread_local char g_last_error[512] = "";
 static std::atomic<long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 void record_cuda_error(cudaError_t e, const char *what, const char *file, int line)
 {
@@ -68,7 +70,6 @@ int read_dev_error(lsg_ctx *c, cudaStream_t s)
 // setup stays recorded (the factors are not valid).
 int clear_dev_error(lsg_ctx *c, cudaStream_t s)
 {
-    c->stream = s;  // the stream lsg_destroy orders the release after
     if (c->setup_status != LSG_OK) return LSG_OK;
     LSG_CK(cudaMemsetAsync(c->err, 0, sizeof(int), s));
     return LSG_OK;
@@ -205,6 +206,10 @@ static void free_ctx(lsg_ctx *c, cudaStream_t s)
     cudaGetLastError();
     release_pinned_state(c->st_host);
     prof_destroy(c);
+    if (c->graph) {
+        pcg_graph_destroy(*c->graph);
+        delete c->graph;
+    }
     delete c;
 }
 
@@ -301,6 +306,7 @@ int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, con
     c->precision = precision;
     c->flags = flags;
     c->wait_budget = kSpinBudgetCycles;
+    for (int i = 0; i < 3; ++i) c->xf_fwd[i] = c->xf_bwd[i] = -1;
     if (flags & LSG_SETUP_PROFILE) prof_create(c);
     LSG_CK(cudaGetDevice(&c->device));
     {
@@ -392,6 +398,10 @@ int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, con
     if (cudaMemsetAsync(c->err, 0, sizeof(int) * 4, s) != cudaSuccess) return fail(LSG_ERR_CUDA);
     st = build_tables(c, da, db, s);
     if (st != LSG_OK) return fail(st);
+    if (!tile_table_lookup(c) && (flags & LSG_SETUP_AUTOTUNE)) {
+        st = autotune_transforms(c, 5, s);
+        if (st != LSG_OK) return fail(st);
+    }
     st = build_tc_tables(c, s);
     if (st != LSG_OK) return fail(st);
     int derr = read_dev_error(c, s);
@@ -426,6 +436,7 @@ int lsg_load_vector(lsg_ctx *c, const double *f, double *F, lsg_stream_t stream)
     if (!c || !f || !F) return LSG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const double *df;
+    c->stream = s;  // lsg_destroy orders the release after the last call's stream
     LSG_TRY(clear_dev_error(c, s));
     LSG_TRY(stage_in(f, c->g.nq, c->fs, &df, s));
     bool hF = !is_device_ptr(F);
@@ -442,6 +453,7 @@ int lsg_apply_A_lowp(lsg_ctx *c, const float *x, float *y, lsg_stream_t stream)
 {
     if (!c || !x || !y || x == y || c->precision == LSG_FP64) return LSG_ERR_ARG;
     if (!is_device_ptr(x) || !is_device_ptr(y)) return LSG_ERR_ARG;
+    c->stream = (cudaStream_t)stream;
     LSG_TRY(clear_dev_error(c, (cudaStream_t)stream));
     LSG_TRY(apply_K_tc(c, x, y, nullptr, (cudaStream_t)stream));
     return read_dev_error(c, (cudaStream_t)stream);
@@ -452,6 +464,7 @@ int lsg_apply_A(lsg_ctx *c, const double *x, double *y, lsg_stream_t stream)
     if (!c || !x || !y || x == y) return LSG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const double *dx;
+    c->stream = s;  // lsg_destroy orders the release after the last call's stream
     LSG_TRY(clear_dev_error(c, s));
     LSG_TRY(stage_in(x, c->g.n, c->xs, &dx, s));
     bool hy = !is_device_ptr(y);
@@ -469,6 +482,7 @@ int lsg_apply_Minv(lsg_ctx *c, const double *r, double *z, lsg_stream_t stream)
     if (!c || !r || !z || r == z) return LSG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const double *dr;
+    c->stream = s;  // lsg_destroy orders the release after the last call's stream
     LSG_TRY(clear_dev_error(c, s));
     LSG_TRY(stage_in(r, c->g.n, c->xs, &dr, s));
     bool hz = !is_device_ptr(z);
@@ -488,6 +502,7 @@ int lsg_pcg_solve(lsg_ctx *c, const double *F, double *u, double rtol, int kmax,
     if (!c || !F || !u || !(rtol >= 0.0) || kmax < 0) return LSG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const double *dF;
+    c->stream = s;  // lsg_destroy orders the release after the last call's stream
     LSG_TRY(clear_dev_error(c, s));
     LSG_TRY(stage_in(F, c->g.n, c->fs, &dF, s));
     bool hu = !is_device_ptr(u);
@@ -515,6 +530,7 @@ int lsg_eval(lsg_ctx *c, const double *u, double *vals, lsg_stream_t stream)
     if (!c || !u || !vals) return LSG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const double *du;
+    c->stream = s;  // lsg_destroy orders the release after the last call's stream
     LSG_TRY(clear_dev_error(c, s));
     LSG_TRY(stage_in(u, c->g.n, c->xs, &du, s));
     bool hv = !is_device_ptr(vals);
@@ -606,6 +622,33 @@ long long lsg_query(lsg_ctx *c, int item)
     case LSG_Q_KX_LO_CALLS: return prof_query(c, PROF_KX_LO, true);
     default: return -1;
     }
+}
+
+int lsg_autotune_transforms(lsg_ctx *c, int reps, int *choice)
+{
+    if (!c) return LSG_ERR_ARG;
+    LSG_TRY(autotune_transforms(c, reps, c->stream));
+    if (c->graph) c->graph->reset();  // a captured solve holds the old launches
+    if (choice)
+        for (int i = 0; i < 3; ++i) choice[i] = c->xf_fwd[i], choice[3 + i] = c->xf_bwd[i];
+    return LSG_OK;
+}
+
+int lsg_transform_tiles(lsg_ctx *c, int *choice)
+{
+    if (!c || !choice) return LSG_ERR_ARG;
+    for (int i = 0; i < 3; ++i) choice[i] = c->xf_fwd[i], choice[3 + i] = c->xf_bwd[i];
+    return LSG_OK;
+}
+
+int lsg_set_transform_tiles(lsg_ctx *c, const int *choice)
+{
+    if (!c || !choice) return LSG_ERR_ARG;
+    for (int i = 0; i < 6; ++i)
+        if (choice[i] < -1 || choice[i] > 4) return LSG_ERR_ARG;
+    for (int i = 0; i < 3; ++i) c->xf_fwd[i] = (signed char)choice[i], c->xf_bwd[i] = (signed char)choice[3 + i];
+    if (c->graph) c->graph->reset();  // a captured solve holds the old launches
+    return LSG_OK;
 }
 
 int lsg_set_wait_budget(lsg_ctx *c, long long cycles)

@@ -1,7 +1,10 @@
 // batch.cu -- batched PCG over many independent problems (uneven sizes).
-// Every problem runs Algorithm 1 on its own stream; the host advances all runs
-// without blocking on any one of them, so the kernels of different problems
-// overlap on the device and each problem stops at its own tolerance.  Mixed-
+// FP64: all problems run as one CUDA graph, one branch per problem, each with
+// Algorithm 1's loop in a conditional WHILE node on the device, so the kernels
+// of different problems overlap and each problem stops at its own tolerance
+// with a single launch and a single wait for the whole batch.  If the graph
+// cannot be built, every problem runs on its own stream and the host advances
+// all runs without blocking on any one of them.  Mixed-
 // precision contexts (FP64 refinement around an FP32 inner PCG, whose steps
 // need host decisions between refinements) run as concurrent solves, one host
 // thread and stream each, a bounded number at a time.
@@ -56,9 +59,60 @@ extern "C" int lsg_batch_solve(int count, lsg_ctx *const *ctxs, const double *co
     for (int i = 0; i < count; ++i)
         if (!ctxs[i] || !F[i] || !u[i]) return LSG_ERR_ARG;
     cudaStream_t s0 = (cudaStream_t)stream;
+    for (int i = 0; i < count; ++i) ctxs[i]->stream = s0;  // lsg_destroy orders the release on it
     bool mixed = false;
     for (int i = 0; i < count; ++i) mixed = mixed || ctxs[i]->precision != LSG_FP64;
-    if (mixed) return batch_concurrent(count, ctxs, F, u, rtol, kmax, infos, s0);
+    if (mixed) {
+        const int st = batch_concurrent(count, ctxs, F, u, rtol, kmax, infos, s0);
+        for (int i = 0; i < count; ++i) ctxs[i]->stream = s0;  // the solves ran on streams that are gone
+        return st;
+    }
+    {
+        // FP64: every problem's solve in one CUDA graph (one branch per problem, each with
+        // its iteration loop in a conditional WHILE node), launched once on the caller's
+        // stream; host arrays are staged in the contexts' buffers around it
+        std::vector<const double *> gF(count);
+        std::vector<double *> gx(count);
+        std::vector<bool> hu(count, false);
+        int st = LSG_OK;
+        for (int i = 0; i < count && st == LSG_OK; ++i) {
+            lsg_ctx *c = ctxs[i];
+            const size_t bytes = sizeof(double) * (size_t)c->g.n;
+            gF[i] = F[i];
+            if (!is_device_ptr(F[i])) {
+                if (cudaMemcpyAsync(c->fs, F[i], bytes, cudaMemcpyHostToDevice, s0) != cudaSuccess) st = LSG_ERR_CUDA;
+                gF[i] = c->fs;
+            }
+            gx[i] = u[i];
+            hu[i] = !is_device_ptr(u[i]);
+            if (hu[i]) {
+                if (cudaMemcpyAsync(c->xs, u[i], bytes, cudaMemcpyHostToDevice, s0) != cudaSuccess) st = LSG_ERR_CUDA;
+                gx[i] = c->xs;
+            }
+        }
+        if (st == LSG_OK) {
+            PcgGraph G;
+            st = pcg_graph_build(G, count, ctxs, gF.data(), gx.data());
+            if (st == LSG_OK) {
+                std::vector<int> status(count, LSG_OK);
+                std::vector<lsg_info> inf(count);
+                st = pcg_graph_run(G, ctxs, rtol, kmax, s0, inf.data(), status.data());
+                for (int i = 0; i < count; ++i) {
+                    if (infos) infos[i] = inf[i];
+                    if (hu[i] && cudaMemcpyAsync(u[i], gx[i], sizeof(double) * (size_t)ctxs[i]->g.n,
+                                                 cudaMemcpyDeviceToHost, s0) != cudaSuccess)
+                        st = LSG_ERR_CUDA;
+                }
+                if (cudaStreamSynchronize(s0) != cudaSuccess) st = LSG_ERR_CUDA;
+                pcg_graph_destroy(G);
+                return st;
+            }
+            pcg_graph_destroy(G);
+            cudaGetLastError();
+        }
+        if (st != LSG_OK && st != LSG_ERR_CUDA) return st;
+        // the graph could not be built: the host-driven interleaving below
+    }
     std::vector<cudaStream_t> st(count, nullptr);
     std::vector<PcgRun> runs(count);
     std::vector<bool> fin(count, false), hostu(count, false);

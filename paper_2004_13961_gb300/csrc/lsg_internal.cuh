@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "lsg.h"
 
 namespace lsg {
@@ -56,6 +58,22 @@ struct PcgState {
     double rho, rho_old, alpha, beta, pw, rr, nF2, eps2, tr;  // tr: true residual^2 scratch
     int k, kmax, done, status;
     int pad[4];
+};
+
+// A PCG solve (or several, one branch each) captured as one CUDA graph with the
+// iteration loop in a conditional WHILE node (pcg.cu).
+struct PcgGraph {
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr, body = nullptr;  // capture streams
+    std::vector<cudaStream_t> branch;            // one per solve (several solves)
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    std::vector<long long> body_launches;        // kernels per loop pass of each solve
+    long long fixed_launches = 0;                // kernels outside the loops
+    int nctx = 0;
+    const double *F0 = nullptr;                  // single solve: the vectors it was captured on
+    double *x0 = nullptr;
+    void reset();
 };
 
 // stages timed by the optional per-context profiler (LSG_SETUP_PROFILE)
@@ -117,6 +135,9 @@ struct lsg_ctx {
     // setup stage times (milliseconds, CUDA events): tables, assembly, ILU(0)
     float t_tables_ms, t_assemble_ms, t_ilu_ms;
     lsg::Prof *prof;           // solve-stage event timing (null unless LSG_SETUP_PROFILE)
+    signed char xf_fwd[3], xf_bwd[3];  // tile variant of each FP64 contraction of K x (-1: default)
+    lsg::PcgGraph *graph;      // the captured FP64 solve (pcg_fp64), built on first use
+    int no_graph;              // capture failed once: solves use the host-driven loop
 };
 
 namespace lsg {
@@ -164,15 +185,23 @@ void pcg_info(const PcgRun &R, lsg_info *info);
 void pcg_release(PcgRun &R);
 int pcg_mixed(lsg_ctx *c, const double *F, double *u, double rtol, int kmax, lsg_info *info,
               cudaStream_t s);
+int pcg_graph_build(PcgGraph &G, int count, lsg_ctx *const *ctxs, const double *const *F, double *const *x);
+int pcg_graph_run(PcgGraph &G, lsg_ctx *const *ctxs, double rtol, int kmax, cudaStream_t s, lsg_info *infos,
+                  int *status);
+void pcg_graph_destroy(PcgGraph &G);
 int read_dev_error(lsg_ctx *c, cudaStream_t s);
 int clear_dev_error(lsg_ctx *c, cudaStream_t s);
 int check_finite(lsg_ctx *c, const double *v, long long n, cudaStream_t s);
 size_t workspace_elems(const Geom &g);
+bool tile_table_lookup(lsg_ctx *c);
+int autotune_transforms(lsg_ctx *c, int reps, cudaStream_t s);
 int gauss_rule(int Q, double *x, double *w, cudaStream_t s);
 long long structural_nnz(const Geom &g);
 
 // host-side count of kernel launches issued by the library (all contexts)
 void count_launch();
+void count_launches(long long k);  // adjusts the count (kernels run inside CUDA graphs)
+long long launches_so_far();
 
 // optional stage timing (no-ops when the context was set up without LSG_SETUP_PROFILE)
 void prof_create(lsg_ctx *c);

@@ -359,9 +359,221 @@ void pcg_release(PcgRun &R)
     R.ev = nullptr;
 }
 
+// ---------------------------------------------------------------------------
+// Algorithm 1 as one CUDA graph.  The loop runs on the device: a conditional WHILE
+// node whose body is one iteration (the same kernels as above) ends with a
+// one-thread kernel that sets the loop condition from the device-side stop test,
+// so nothing is launched past convergence and the host waits once per solve.
+
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const PcgState *st)
+{
+    cudaGraphSetConditional(h, st->done ? 0u : 1u);
+}
+
+// Appends one solve to the graph being captured on stream s: the state upload from
+// the pinned mirror (read when the graph runs), r = F - K x, the WHILE node with one
+// iteration in its body (captured on the helper stream bs), the true residual and
+// the state download.  *body_launches: kernels per loop pass.
+static int capture_pcg(lsg_ctx *c, const double *F, double *x, cudaStream_t s, cudaStream_t bs,
+                       long long *body_launches)
+{
+    const long long n = c->g.n;
+    LSG_CK(cudaMemcpyAsync(c->st, c->st_host, sizeof(PcgState), cudaMemcpyHostToDevice, s));
+    LSG_CK(cudaMemsetAsync(c->counters + 4, 0, sizeof(unsigned), s));
+    LSG_TRY(clear_dev_error(c, s));
+    LSG_TRY(apply_K(c, x, c->wv, nullptr, s));
+    ::lsg::count_launch();
+    k_init<<<kRedBlocks, kRedThreads, 0, s>>>(n, F, c->wv, c->r, c->red, c->counters + 4, c->st);
+    LSG_CK(cudaGetLastError());
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    LSG_CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphConditionalHandle h;
+    LSG_CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    ::lsg::count_launch();
+    k_loop_cond<<<1, 1, 0, s>>>(h, c->st);
+    LSG_CK(cudaGetLastError());
+    LSG_CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    LSG_CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
+    LSG_CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    LSG_CK(cudaStreamBeginCaptureToGraph(bs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeRelaxed));
+    const long long l0 = launches_so_far();
+    int st = iteration(c, x, bs);
+    if (st == LSG_OK) {
+        ::lsg::count_launch();
+        k_loop_cond<<<1, 1, 0, bs>>>(h, c->st);
+        if (cudaGetLastError() != cudaSuccess) st = LSG_ERR_CUDA;
+    }
+    *body_launches = launches_so_far() - l0;
+    cudaGraph_t body = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(bs, &body);
+    LSG_TRY(st);
+    LSG_CK(e);
+    LSG_TRY(apply_K(c, x, c->wv, nullptr, s));
+    ::lsg::count_launch();
+    k_true<<<kRedBlocks, kRedThreads, 0, s>>>(n, F, c->wv, c->red, c->counters + 4, c->st);
+    LSG_CK(cudaGetLastError());
+    LSG_CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    LSG_CK(cudaMemcpyAsync(&c->st_host->pad[0], c->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    return LSG_OK;
+}
+
+void PcgGraph::reset()
+{
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    nctx = 0;
+}
+
+// Captures `count` solves (context i on F[i], x[i]) into one graph, each on its own
+// branch forked from the capture stream, and instantiates it.
+int pcg_graph_build(PcgGraph &G, int count, lsg_ctx *const *ctxs, const double *const *F, double *const *x)
+{
+    G.reset();
+    if (!G.cap) LSG_CK(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking));
+    if (!G.body) LSG_CK(cudaStreamCreateWithFlags(&G.body, cudaStreamNonBlocking));
+    if ((int)G.branch.size() < count) {
+        const size_t old = G.branch.size();
+        G.branch.resize(count, nullptr);
+        for (size_t i = old; i < G.branch.size(); ++i)
+            LSG_CK(cudaStreamCreateWithFlags(&G.branch[i], cudaStreamNonBlocking));
+    }
+    if (!G.fork) LSG_CK(cudaEventCreateWithFlags(&G.fork, cudaEventDisableTiming));
+    if (G.join.size() < (size_t)count) {
+        const size_t old = G.join.size();
+        G.join.resize(count, nullptr);
+        for (size_t i = old; i < G.join.size(); ++i)
+            LSG_CK(cudaEventCreateWithFlags(&G.join[i], cudaEventDisableTiming));
+    }
+    const long long l0 = launches_so_far();
+    LSG_CK(cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeRelaxed));
+    int st = LSG_OK;
+    cudaError_t e = cudaEventRecord(G.fork, G.cap);
+    if (e != cudaSuccess) st = LSG_ERR_CUDA;
+    G.body_launches.assign(count, 0);
+    for (int i = 0; i < count && st == LSG_OK; ++i) {
+        cudaStream_t b = count == 1 ? G.cap : G.branch[i];
+        if (count > 1 && cudaStreamWaitEvent(b, G.fork, 0) != cudaSuccess) st = LSG_ERR_CUDA;
+        if (st == LSG_OK) st = capture_pcg(ctxs[i], F[i], x[i], b, G.body, &G.body_launches[i]);
+        if (st == LSG_OK && count > 1 &&
+            (cudaEventRecord(G.join[i], b) != cudaSuccess || cudaStreamWaitEvent(G.cap, G.join[i], 0) != cudaSuccess))
+            st = LSG_ERR_CUDA;
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(G.cap, &graph);
+    if (st == LSG_OK && e != cudaSuccess) {
+        record_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+        st = LSG_ERR_CUDA;
+    }
+    if (st == LSG_OK) {
+        e = cudaGraphInstantiate(&G.exec, graph, 0);
+        if (e != cudaSuccess) {
+            record_cuda_error(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+            G.exec = nullptr;
+            st = LSG_ERR_CUDA;
+        }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    // kernels count when the graph runs, not when they are captured
+    long long body = 0;
+    for (long long b : G.body_launches) body += b;
+    G.fixed_launches = launches_so_far() - l0 - body;
+    count_launches(-(launches_so_far() - l0));
+    G.nctx = st == LSG_OK ? count : 0;
+    return st;
+}
+
+// Runs a built graph on stream s with the given tolerance and iteration limit, and
+// waits for it.  infos/status per context.
+int pcg_graph_run(PcgGraph &G, lsg_ctx *const *ctxs, double rtol, int kmax, cudaStream_t s, lsg_info *infos,
+                  int *status)
+{
+    for (int i = 0; i < G.nctx; ++i) {
+        PcgState *h = ctxs[i]->st_host;
+        *h = PcgState{};
+        h->eps2 = rtol * rtol;
+        h->kmax = kmax;
+    }
+    LSG_CK(cudaGraphLaunch(G.exec, s));
+    LSG_CK(cudaStreamSynchronize(s));
+    long long runs = G.fixed_launches;
+    int first = LSG_OK;
+    for (int i = 0; i < G.nctx; ++i) {
+        const PcgState *h = ctxs[i]->st_host;
+        int st = h->status;
+        if (st == LSG_OK && !(h->rr <= h->eps2 * h->nF2)) st = LSG_ERR_NOT_CONVERGED;
+        const int derr = dev_err_status(h->pad[0]);
+        if (derr != LSG_OK) st = derr;
+        // the body ran once per completed pass, plus the pass that found p^T w <= 0
+        runs += G.body_launches[i] * (long long)(h->k + (h->status != LSG_OK ? 1 : 0));
+        if (infos) {
+            lsg_info &in = infos[i];
+            in.iters = h->k;
+            in.outer_iters = 0;
+            const double nF = sqrt(h->nF2);
+            in.relres = nF > 0 ? sqrt(h->rr) / nF : sqrt(h->rr);
+            in.relres_true = nF > 0 ? sqrt(h->tr) / nF : sqrt(h->tr);
+            in.status = st;
+        }
+        if (status) status[i] = st;
+        if (st != LSG_OK && first == LSG_OK) first = st;
+    }
+    count_launches(runs);
+    return first;
+}
+
+void pcg_graph_destroy(PcgGraph &G)
+{
+    G.reset();
+    for (cudaStream_t b : G.branch)
+        if (b) cudaStreamDestroy(b);
+    G.branch.clear();
+    for (cudaEvent_t e : G.join)
+        if (e) cudaEventDestroy(e);
+    G.join.clear();
+    if (G.fork) cudaEventDestroy(G.fork);
+    if (G.cap) cudaStreamDestroy(G.cap);
+    if (G.body) cudaStreamDestroy(G.body);
+    G.fork = nullptr;
+    G.cap = G.body = nullptr;
+}
+
 // PCG on device-resident F and x (x: initial guess in, iterate out); blocking.
+// Contexts set up with LSG_SETUP_PROFILE run the host-driven loop (its per-kernel
+// events cannot be recorded inside a graph's loop); the others run the solve as one
+// graph, captured once per (F, x) pair and kept with the context.
 int pcg_fp64(lsg_ctx *c, const double *F, double *x, double rtol, int kmax, lsg_info *info, cudaStream_t s)
 {
+    if (!c->prof && !c->no_graph) {
+        if (!c->graph) c->graph = new PcgGraph();
+        PcgGraph &G = *c->graph;
+        int st = LSG_OK;
+        if (!G.exec || G.F0 != F || G.x0 != x) {
+            st = pcg_graph_build(G, 1, &c, &F, &x);
+            G.F0 = F;
+            G.x0 = x;
+        }
+        if (st == LSG_OK) {
+            int status = LSG_OK;
+            lsg_info tmp;
+            st = pcg_graph_run(G, &c, rtol, kmax, s, &tmp, &status);
+            if (info) *info = tmp;
+            return st == LSG_OK ? status : st;
+        }
+        // the graph could not be built: use the host-driven loop from now on
+        c->no_graph = 1;
+        G.reset();
+    }
     PcgRun R{};
     int st = pcg_start(R, c, F, x, rtol, kmax, s);
     bool fin = false;

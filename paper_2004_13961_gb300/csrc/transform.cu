@@ -259,30 +259,49 @@ static void add_out(XfJob<T> &j, typename ident<T>::type *y, const typename iden
     o.t[1] = XfTerm<T>{x1, t1};
 }
 
-template <typename T>
-static int launch_fwd(const XfJob<T> &j, cudaStream_t s)
+// Tile shapes of the contractions: (rows of the output per CTA, batch columns per
+// CTA), 16 x 16 threads each computing (rows/16) x (columns/16) outputs of both
+// parity halves.  Which one runs for each contraction of K x is chosen per problem
+// size by the autotuner (lsg_autotune_transforms) or taken from its committed table;
+// variant -1 is the fixed default.
+template <typename T, int TA, int TB>
+static void fwd_v(const XfJob<T> &j, cudaStream_t s)
 {
-    constexpr int TP = 32, TB = 64, TK = 16;
-    dim3 grid((j.Qh + TP - 1) / TP, (unsigned)((j.B + TB - 1) / TB), j.nout);
+    dim3 grid((j.Qh + TA - 1) / TA, (unsigned)((j.B + TB - 1) / TB), j.nout);
+    k_xf_fwd<T, TA, TB, 16><<<grid, XT, 0, s>>>(j);
+}
+template <typename T, int TA, int TB>
+static void bwd_v(const XfJob<T> &j, cudaStream_t s)
+{
+    const int ne = (j.n1 + 1) / 2;
+    dim3 grid((ne + TA - 1) / TA, (unsigned)((j.B + TB - 1) / TB), j.nout);
+    k_xf_bwd<T, TA, TB, 16><<<grid, XT, 0, s>>>(j);
+}
+template <typename T>
+static int launch_fwd(const XfJob<T> &j, cudaStream_t s, int v = -1)
+{
     ::lsg::count_launch();
-    k_xf_fwd<T, TP, TB, TK><<<grid, XT, 0, s>>>(j);
+    switch (v) {
+    case 0: fwd_v<T, 16, 16>(j, s); break;
+    case 1: fwd_v<T, 16, 32>(j, s); break;
+    case 2: fwd_v<T, 32, 32>(j, s); break;
+    case 4: fwd_v<T, 64, 32>(j, s); break;
+    default: fwd_v<T, 32, 64>(j, s); break;  // variant 3, the default
+    }
     LSG_CK(cudaGetLastError());
     return LSG_OK;
 }
 template <typename T>
-static int launch_bwd(const XfJob<T> &j, cudaStream_t s)
+static int launch_bwd(const XfJob<T> &j, cudaStream_t s, int v = -1)
 {
-    int ne = (j.n1 + 1) / 2;
-    if (j.B >= 2048) {
-        constexpr int TM = 32, TB = 64, TK = 16;
-        dim3 grid((ne + TM - 1) / TM, (unsigned)((j.B + TB - 1) / TB), j.nout);
-        ::lsg::count_launch();
-        k_xf_bwd<T, TM, TB, TK><<<grid, XT, 0, s>>>(j);
-    } else {
-        constexpr int TM = 32, TB = 32, TK = 16;
-        dim3 grid((ne + TM - 1) / TM, (unsigned)((j.B + TB - 1) / TB), j.nout);
-        ::lsg::count_launch();
-        k_xf_bwd<T, TM, TB, TK><<<grid, XT, 0, s>>>(j);
+    if (v < 0) v = j.B >= 2048 ? 3 : 2;  // the default
+    ::lsg::count_launch();
+    switch (v) {
+    case 0: bwd_v<T, 16, 16>(j, s); break;
+    case 1: bwd_v<T, 16, 32>(j, s); break;
+    case 2: bwd_v<T, 32, 32>(j, s); break;
+    case 4: bwd_v<T, 64, 32>(j, s); break;
+    default: bwd_v<T, 32, 64>(j, s); break;
     }
     LSG_CK(cudaGetLastError());
     return LSG_OK;
@@ -305,15 +324,16 @@ static int apply_K_t(lsg_ctx *c, const T *x, T *y, const int *done, T *ws, const
     const Geom &g = c->g;
     const long long Q = g.Q, n1 = g.n1;
     XfJob<T> j;
+    const signed char *vf = c->xf_fwd, *vb = c->xf_bwd;  // tile variant of each contraction
     if (g.d == 1) {
         T *H = ws, *Gx = ws + Q;
         job_init(j, c, 1, done);
         add_out(j, H, Wb, x, 0);
         add_out(j, Gx, Wa, x, 1);
-        LSG_TRY(launch_fwd(j, s));
+        LSG_TRY(launch_fwd(j, s, vf[0]));
         job_init(j, c, 1, done);
         add_out(j, y, nullptr, H, 0, Gx, 1);
-        return launch_bwd(j, s);
+        return launch_bwd(j, s, vb[0]);
     }
     if (g.d == 2) {
         T *AP = ws, *AD = ws + Q * n1;           // [Q][n1]
@@ -322,19 +342,19 @@ static int apply_K_t(lsg_ctx *c, const T *x, T *y, const int *done, T *ws, const
         job_init(j, c, n1, done);                     // contract x: U[j][k]
         add_out(j, AP, nullptr, x, 0);
         add_out(j, AD, nullptr, x, 1);
-        LSG_TRY(launch_fwd(j, s));
+        LSG_TRY(launch_fwd(j, s, vf[0]));
         job_init(j, c, Q, done);                      // contract y: A[q][j]
         add_out(j, H, Wb, AP, 0);
         add_out(j, Gy, Wa, AP, 1);
         add_out(j, Gx, Wa, AD, 0);
-        LSG_TRY(launch_fwd(j, s));
+        LSG_TRY(launch_fwd(j, s, vf[1]));
         job_init(j, c, Q, done);                      // contract x-nodes: [r][q]
         add_out(j, P1, nullptr, H, 0, Gx, 1);
         add_out(j, P2, nullptr, Gy, 0);
-        LSG_TRY(launch_bwd(j, s));
+        LSG_TRY(launch_bwd(j, s, vb[0]));
         job_init(j, c, n1, done);                     // contract y-nodes: [m][r]
         add_out(j, y, nullptr, P1, 0, P2, 1);
-        return launch_bwd(j, s);
+        return launch_bwd(j, s, vb[1]);
     }
     // d == 3
     T *A0 = ws, *A1 = ws + Q * n1 * n1;                       // [Q][n1][n1]
@@ -344,32 +364,32 @@ static int apply_K_t(lsg_ctx *c, const T *x, T *y, const int *done, T *ws, const
     job_init(j, c, n1 * n1, done);                 // x: U[l][j][k] -> [q][l][j]
     add_out(j, A0, nullptr, x, 0);
     add_out(j, A1, nullptr, x, 1);
-    LSG_TRY(launch_fwd(j, s));
+    LSG_TRY(launch_fwd(j, s, vf[0]));
     job_init(j, c, Q * n1, done);                  // y: [q][l][j] -> [r][q][l]
     add_out(j, B0, nullptr, A0, 0);                // phi_x phi_y
     add_out(j, B1, nullptr, A0, 1);                // phi_x phi'_y
     add_out(j, B2, nullptr, A1, 0);                // phi'_x phi_y
-    LSG_TRY(launch_fwd(j, s));
+    LSG_TRY(launch_fwd(j, s, vf[1]));
     job_init(j, c, Q * Q, done);                   // z: [r][q][l] -> [s][r][q]
     add_out(j, H, Wb, B0, 0);
     add_out(j, Gz, Wa, B0, 1);
     add_out(j, Gy, Wa, B1, 0);
     add_out(j, Gx, Wa, B2, 0);
-    LSG_TRY(launch_fwd(j, s));
+    LSG_TRY(launch_fwd(j, s, vf[2]));
     T *Pa = B0, *Pb = B1, *Pc = B2;           // [n1][Q][Q] = [m][s][r]
     job_init(j, c, Q * Q, done);
     add_out(j, Pa, nullptr, H, 0, Gx, 1);
     add_out(j, Pb, nullptr, Gy, 0);
     add_out(j, Pc, nullptr, Gz, 0);
-    LSG_TRY(launch_bwd(j, s));
+    LSG_TRY(launch_bwd(j, s, vb[0]));
     T *Ra = A0, *Rc = A1;                     // [n1][n1][Q] = [n'][m][s]
     job_init(j, c, n1 * Q, done);
     add_out(j, Ra, nullptr, Pa, 0, Pb, 1);
     add_out(j, Rc, nullptr, Pc, 0);
-    LSG_TRY(launch_bwd(j, s));
+    LSG_TRY(launch_bwd(j, s, vb[1]));
     job_init(j, c, n1 * n1, done);                 // [l'][n'][m]
     add_out(j, y, nullptr, Ra, 0, Rc, 1);
-    return launch_bwd(j, s);
+    return launch_bwd(j, s, vb[2]);
 }
 
 int apply_K(lsg_ctx *c, const double *x, double *y, const int *done, cudaStream_t s)
@@ -451,6 +471,98 @@ int eval_grid(lsg_ctx *c, const double *u, double *vals, cudaStream_t s)
     job_init(j, c, Q * Q, nullptr);
     add_out(j, vals, nullptr, Bv, 0);
     return launch_fwd(j, s);
+}
+
+}  // namespace lsg
+
+// ---------------------------------------------------------------------------
+// Autotuner of the contraction tiles.  K x is d forward and d backward
+// contractions whose shapes (output rows x batch columns) depend on N and Q; for
+// each one in turn it times K x with every tile variant (the other contractions
+// at their current choice), keeps the fastest, and repeats the sweep once.  The
+// results for the sizes the workloads use are committed in xf_tiles_gb300.inc
+// (written by paper_2004_13961_gb300/autotune.py on a GB300) and applied at
+// setup; other sizes keep the default unless the context asks to be tuned.
+#include <map>
+#include <mutex>
+#include <tuple>
+
+namespace lsg {
+
+namespace {
+struct TileRow {
+    int d, N, Q;
+    signed char f[3], b[3];
+};
+const TileRow kTileTable[] = {
+#include "xf_tiles_gb300.inc"
+    {0, 0, 0, {-1, -1, -1}, {-1, -1, -1}}};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, TileRow> g_tuned;  // sizes tuned in this process
+}  // namespace
+
+bool tile_table_lookup(lsg_ctx *c)
+{
+    const Geom &g = c->g;
+    auto apply = [&](const TileRow &r) {
+        for (int i = 0; i < 3; ++i) c->xf_fwd[i] = r.f[i], c->xf_bwd[i] = r.b[i];
+    };
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(std::make_tuple(g.d, g.N, g.Q));
+        if (it != g_tuned.end()) {
+            apply(it->second);
+            return true;
+        }
+    }
+    for (const TileRow &r : kTileTable)
+        if (r.d == g.d && r.N == g.N && r.Q == g.Q) {
+            apply(r);
+            return true;
+        }
+    return false;
+}
+
+int autotune_transforms(lsg_ctx *c, int reps, cudaStream_t s)
+{
+    const Geom &g = c->g;
+    if (reps < 1) reps = 5;
+    double *x = c->xs, *y = c->ys;
+    LSG_CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)g.n, s));
+    cudaEvent_t e0, e1;
+    LSG_CK(cudaEventCreate(&e0));
+    LSG_CK(cudaEventCreate(&e1));
+    auto time_kx = [&](float *ms) -> int {
+        LSG_TRY(apply_K(c, x, y, nullptr, s));  // warm-up
+        LSG_CK(cudaEventRecord(e0, s));
+        for (int r = 0; r < reps; ++r) LSG_TRY(apply_K(c, x, y, nullptr, s));
+        LSG_CK(cudaEventRecord(e1, s));
+        LSG_CK(cudaEventSynchronize(e1));
+        LSG_CK(cudaEventElapsedTime(ms, e0, e1));
+        return LSG_OK;
+    };
+    int st = LSG_OK;
+    for (int pass = 0; pass < 2 && st == LSG_OK; ++pass)
+        for (int k = 0; k < 2 * g.d && st == LSG_OK; ++k) {
+            signed char *slot = k < g.d ? &c->xf_fwd[k] : &c->xf_bwd[k - g.d];
+            signed char best = *slot;
+            float tbest = 0.f;
+            st = time_kx(&tbest);
+            for (int v = 0; v < 5 && st == LSG_OK; ++v) {
+                *slot = (signed char)v;
+                float t = 0.f;
+                st = time_kx(&t);
+                if (st == LSG_OK && t < tbest) tbest = t, best = (signed char)v;
+            }
+            *slot = best;
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != LSG_OK) return st;
+    TileRow r{g.d, g.N, g.Q, {c->xf_fwd[0], c->xf_fwd[1], c->xf_fwd[2]}, {c->xf_bwd[0], c->xf_bwd[1], c->xf_bwd[2]}};
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[std::make_tuple(g.d, g.N, g.Q)] = r;
+    return LSG_OK;
 }
 
 }  // namespace lsg

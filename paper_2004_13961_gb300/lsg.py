@@ -22,6 +22,7 @@ from . import build as _build
 FP64, MIXED_TF32, MIXED_BF16 = 0, 1, 2
 SETUP_KEEP_M = 1
 SETUP_PROFILE = 2
+SETUP_AUTOTUNE = 4
 
 EXPORT_GAUSS_X, EXPORT_GAUSS_W, EXPORT_AHAT, EXPORT_BHAT = 0, 1, 2, 3
 EXPORT_BAND_S, EXPORT_BAND_M, EXPORT_M, EXPORT_LU = 4, 5, 6, 7
@@ -40,6 +41,7 @@ SYMBOLS = [
     "lsg_setup", "lsg_setup_ex", "lsg_load_vector", "lsg_apply_A", "lsg_apply_A_lowp", "lsg_apply_Minv",
     "lsg_pcg_solve",
     "lsg_eval", "lsg_export_count", "lsg_export", "lsg_query", "lsg_destroy", "lsg_set_wait_budget",
+    "lsg_autotune_transforms", "lsg_transform_tiles", "lsg_set_transform_tiles",
     "lsg_batch_solve",
     "lsg_server_create", "lsg_server_set_aging", "lsg_server_submit", "lsg_server_poll", "lsg_server_drain",
     "lsg_server_release", "lsg_server_destroy",
@@ -106,6 +108,9 @@ def load(build_if_needed: bool = True):
     L.lsg_query.restype = cll
     L.lsg_destroy.argtypes = [vp]
     L.lsg_set_wait_budget.argtypes = [vp, cll]
+    L.lsg_autotune_transforms.argtypes = [vp, ci, ctypes.POINTER(ci)]
+    L.lsg_transform_tiles.argtypes = [vp, ctypes.POINTER(ci)]
+    L.lsg_set_transform_tiles.argtypes = [vp, ctypes.POINTER(ci)]
     L.lsg_batch_solve.argtypes = [ci, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), cd, ci,
                                   ctypes.POINTER(LsgInfo), vp]
     L.lsg_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t, ci]
@@ -194,7 +199,7 @@ class Context:
     """An lsg_ctx: tables, coefficient samples, M's ILU(0) factors and workspaces."""
 
     def __init__(self, d, N, T, a, b, Q=None, precision=FP64, keep_M=False, stream=None, allow_breakdown=False,
-                 profile=False):
+                 profile=False, autotune=False):
         L = load()
         self._L = L
         self.d, self.N, self.T = d, N, T
@@ -202,7 +207,8 @@ class Context:
         self.precision = precision
         h = ctypes.c_void_p(0)
         st = L.lsg_setup_ex(ctypes.byref(h), d, N, T, self.Q, _ptr(a), _ptr(b), precision,
-                            (SETUP_KEEP_M if keep_M else 0) | (SETUP_PROFILE if profile else 0),
+                            (SETUP_KEEP_M if keep_M else 0) | (SETUP_PROFILE if profile else 0)
+                            | (SETUP_AUTOTUNE if autotune else 0),
                             _stream(stream))
         self.status = st
         self._h = h
@@ -282,6 +288,21 @@ class Context:
 
     def query(self, item):
         return int(self._L.lsg_query(self._h, item))
+
+    def autotune_transforms(self, reps=5):
+        """Time the tile shapes of K x's contractions and keep the fastest; returns the choice."""
+        out = (ctypes.c_int * 6)()
+        _check(self._L.lsg_autotune_transforms(self._h, int(reps), out), "lsg_autotune_transforms")
+        return list(out)
+
+    def transform_tiles(self):
+        out = (ctypes.c_int * 6)()
+        _check(self._L.lsg_transform_tiles(self._h, out), "lsg_transform_tiles")
+        return list(out)
+
+    def set_transform_tiles(self, choice):
+        arr = (ctypes.c_int * 6)(*[int(v) for v in choice])
+        _check(self._L.lsg_set_transform_tiles(self._h, arr), "lsg_set_transform_tiles")
 
     def set_wait_budget(self, cycles):
         """Budget (SM clock cycles) of the sweeps' dependency waits; 0 = default."""
