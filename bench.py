@@ -202,29 +202,46 @@ def run_reference(args, world, rank):
 
 # --------------------------------------------------------------------------- native (GPU) leg
 
-def run_batched(lsg, W, torch, dev, world, count=256, precision=None):
+def run_batched(lsg, W, torch, dev, world, count=256, precision=None, threads=8):
     """Config 4: 256 independent 2D problems, N uniform on {32, 48, ..., 256} (seed 21), T=8,
-    PCG to 1e-10 through lsg_batch_solve (FP64: all iterations interleaved on the device;
-    mixed: concurrent refined solves).  Timed: setup of every context (ILU(0) included) plus
-    the batched solve."""
+    PCG to 1e-10 through lsg_batch_solve (FP64: one CUDA graph, every problem's loop on the
+    device; mixed: concurrent refined solves).  Timed: setup of every context (ILU(0)
+    included, `threads` host threads with a stream each) plus the batched solve."""
+    from concurrent.futures import ThreadPoolExecutor
     precision = lsg.FP64 if precision is None else precision
     probs = W.batch_problems(count)
     dofs = sum((p["N"] - 1) ** 2 for p in probs)
     dev_in = [(torch.tensor(p["a"], device=dev), torch.tensor(p["b"], device=dev), torch.tensor(p["f"], device=dev))
               for p in probs]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(threads)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ctxs, Fs, us = [], [], []
-    breakdowns = 0
-    for p, (a, b, f) in zip(probs, dev_in):
-        c = lsg.Context(2, p["N"], p["T"], a, b, allow_breakdown=True, precision=precision)
-        if c.status == lsg.ERR_ILU_BREAKDOWN:  # ILU(0) of this M does not exist: counted, not solved
-            breakdowns += 1
-            c.close()
-            continue
-        Fs.append(c.load_vector(f))
-        us.append(torch.zeros_like(Fs[-1]))
-        ctxs.append(c)
+
+    def setup(k):
+        out = []
+        st = streams[k]
+        for idx in range(k, count, threads):
+            p = probs[idx]
+            a, b, f = dev_in[idx]
+            c = lsg.Context(2, p["N"], p["T"], a, b, allow_breakdown=True, precision=precision, stream=st)
+            if c.status == lsg.ERR_ILU_BREAKDOWN:  # ILU(0) of this M does not exist: counted, not solved
+                c.close()
+                out.append((idx, None, None))
+                continue
+            with torch.cuda.stream(st):
+                F = c.load_vector(f, stream=st)
+                u0 = torch.zeros_like(F)
+            out.append((idx, c, (F, u0)))
+        st.synchronize()
+        return out
+
+    with ThreadPoolExecutor(threads) as ex:
+        parts = [r for part in ex.map(setup, range(threads)) for r in part]
+    parts.sort(key=lambda r: r[0])
+    breakdowns = sum(1 for r in parts if r[1] is None)
+    ctxs = [r[1] for r in parts if r[1] is not None]
+    Fs = [r[2][0] for r in parts if r[1] is not None]
+    us = [r[2][1] for r in parts if r[1] is not None]
     t1 = time.perf_counter()
     st, infos = lsg.batch_solve(ctxs, Fs, us, rtol=1e-10)
     torch.cuda.synchronize()
@@ -237,51 +254,144 @@ def run_batched(lsg, W, torch, dev, world, count=256, precision=None):
                 precision={lsg.FP64: "fp64", lsg.MIXED_TF32: "mixed-tf32", lsg.MIXED_BF16: "mixed-bf16"}[precision],
                 setup_s=t1 - t0, solve_s=t2 - t1, solves_s=world * ok / total,
                 gdof_s=world * dofs / total / 1e9, iters_mean=float(np.mean([i["iters"] for i in infos])),
-                note=("per-problem streams with device-resident PCG state" if precision == lsg.FP64 else
-                      "concurrent refined solves, 8 host threads / streams") + "; setup included")
+                note=("setup on %d host threads; " % threads)
+                + ("one CUDA graph launch, every problem's PCG loop in a device-side WHILE node"
+                   if precision == lsg.FP64 else "concurrent refined solves, 8 host threads / streams"))
 
 
-def run_serving(lsg, W, world, count=32, rate=4.0, precision=None):
-    """A bounded sample of config 5: Poisson arrivals (seed 31), 70% 2D with N log-uniform in
-    [64, 512], 30% 3D with N uniform in [24, 40], T in {4, 8}, a = exp(g) with sigma in
-    [0.5, 2.3]; refined to 1e-10 (mixed TF32, or plain FP64 PCG for comparison); HBM-admitted
-    (64 GB budget, 4 slots, smallest footprint first).  Latency is
-    submit -> solution in host memory; requests whose ILU(0) breaks down are counted."""
-    reqs = W.serving_stream(count, seed=31, rate_hz=rate, n2d=(64, 512), n3d=(24, 40))
+def _serve_once(lsg, W, data, rate_hz, precision, budget, inflight, world):
+    """Submit the requests of `data` with Poisson arrivals at rate_hz (times scaled from the
+    unit-rate draws), drain, and summarise latencies per class."""
+    srv = lsg.Server(budget, max_inflight=inflight)
+    rejected = 0
+    t0 = time.perf_counter()
+    for i, (r, p) in enumerate(data):
+        delay = r["arrival_unit"] / rate_hz - (time.perf_counter() - t0) if rate_hz else 0.0
+        if delay > 0:
+            time.sleep(delay)
+        st = srv.submit(i, r["d"], r["N"], r["T"], p["a"], p["b"], p["f"], precision=precision, rtol=1e-10)
+        if st == lsg.ERR_NOMEM:
+            rejected += 1
+    srv.drain()
+    t1 = time.perf_counter()
+    res = srv.poll(len(data) + 8)
+    srv.close()
+    st = [x["info"]["status"] for x in res]
+    out = dict(requests=len(data), handled=len(res), completed=int(sum(1 for v in st if v == 0)),
+               ilu_breakdown=int(sum(1 for v in st if v == lsg.ERR_ILU_BREAKDOWN)),
+               rejected_over_budget=rejected, other_errors=int(sum(1 for v in st if v not in (0, lsg.ERR_ILU_BREAKDOWN))),
+               wall_s=t1 - t0, arrival_rate_hz=rate_hz)
+    out["solves_s"] = world * out["completed"] / max_over_ranks(t1 - t0, world)
+    out["handled_s"] = out["handled"] / (t1 - t0)
+    lat = np.array([x["latency_ms"] for x in res if x["info"]["status"] == 0])
+    if len(lat):
+        out.update(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)))
+    by = {}
+    for dd in (2, 3):
+        l = np.array([x["latency_ms"] for x in res if x["info"]["status"] == 0 and data[x["id"]][0]["d"] == dd])
+        c = dict(requests=sum(1 for r, _ in data if r["d"] == dd), completed=int(len(l)))
+        if len(l):
+            c.update(p50_ms=float(np.percentile(l, 50)), p99_ms=float(np.percentile(l, 99)))
+        by[f"{dd}d"] = c
+    out["by_class"] = by
+    return out
+
+
+def run_serving(lsg, W, world, precision, count=40, n2d=(64, 1024), n3d=(24, 40), budget_gb=64, inflight=4,
+                fracs=(0.5, 0.8, 0.95), rates=None):
+    """Config 5 (serving) as continuous batching: requests of the mix (70% 2D, N log-uniform in
+    n2d; 30% 3D, N uniform in n3d; T in {4, 8}; a = exp(g) with sigma in [0.5, 2.3]; refined to
+    1e-10) admitted by HBM footprint into `inflight` slots.  First the capacity mu: every
+    request at t = 0, mu = requests handled per second; then Poisson arrivals at 0.5, 0.8 and
+    0.95 mu.  Latency runs from submit to the solution in host memory."""
+    reqs = W.serving_stream(count, seed=31, rate_hz=1.0, n2d=n2d, n3d=n3d)
     data = []
     for r in reqs:
         p = W.random_exp_problem(r["d"], r["N"], r["T"], r["seed"], r["seed"] + 1, r["seed"] + 2, sigma=r["sigma"])
+        r = dict(r, arrival_unit=r["arrival_s"])
         data.append((r, p))
-    srv = lsg.Server(64 << 30, max_inflight=4)
-    t0 = time.perf_counter()
-    for i, (r, p) in enumerate(data):
-        delay = r["arrival_s"] - (time.perf_counter() - t0)
-        if delay > 0:
-            time.sleep(delay)
-        srv.submit(i, r["d"], r["N"], r["T"], p["a"], p["b"], p["f"], precision=precision, rtol=1e-10)
-    srv.drain()
-    t1 = time.perf_counter()
-    res = srv.poll(count + 8)
-    srv.close()
-    lat = np.array([x["latency_ms"] for x in res if x["info"]["status"] == 0])
-    st = [x["info"]["status"] for x in res]
-    by_class = {}
-    for dd in (2, 3):
-        l = np.array([x["latency_ms"] for x in res if x["info"]["status"] == 0 and data[x["id"]][0]["d"] == dd])
-        n_req = sum(1 for r, _ in data if r["d"] == dd)
-        c = dict(requests=n_req, completed=int(len(l)))
-        if len(l):
-            c.update(p50_ms=float(np.percentile(l, 50)), p99_ms=float(np.percentile(l, 99)))
-        by_class[f"{dd}d"] = c
-    out = dict(requests=count, completed=int((np.array(st) == 0).sum()),
-               ilu_breakdown=int((np.array(st) == lsg.ERR_ILU_BREAKDOWN).sum()),
-               other_errors=int(sum(1 for v in st if v not in (0, lsg.ERR_ILU_BREAKDOWN))),
-               wall_s=t1 - t0, solves_s=world * len(lat) / max_over_ranks(t1 - t0, world),
-               precision="mixed-tf32" if precision == lsg.MIXED_TF32 else "fp64", rtol=1e-10,
-               arrival_rate_hz=rate, by_class=by_class,
-               sample=f"{count} requests of the config-5 mix at {rate} Hz, N capped at 512 (2D) and 40 (3D)")
-    if len(lat):
-        out.update(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)))
+    budget = int(budget_gb) << 30
+    sat = _serve_once(lsg, W, data, 0.0, precision, budget, inflight, world)
+    mu = sat["handled_s"]
+    runs = {"saturated": sat}
+    for f in fracs:
+        runs[f"{f:.2f}mu"] = _serve_once(lsg, W, data, f * mu, precision, budget, inflight, world)
+    for name, rate in (rates or {}).items():
+        runs[name] = _serve_once(lsg, W, data, rate, precision, budget, inflight, world)
+    return dict(precision="mixed-tf32" if precision == lsg.MIXED_TF32 else "fp64", rtol=1e-10, capacity_mu=mu,
+                hbm_budget_gb=budget_gb, slots=inflight,
+                sample=(f"{count} requests of the config-5 mix per run (2D N in [{n2d[0]}, {n2d[1]}], 3D N in "
+                        f"[{n3d[0]}, {n3d[1]}]); the same requests at every rate"), runs=runs)
+
+
+def run_serving_large(lsg, W, world, precision, budget_gb=64):
+    """The config-5 sizes at the top of its range, each served alone through the same server:
+    2D N=1024 T=8, 3D N=128 and N=160 with T=4 (sigma 0.5), and 3D N=160 T=8, whose FP32
+    factors (~135 GB) exceed the HBM budget and are rejected at submit (LSG_ERR_NOMEM)."""
+    cases = [(2, 1024, 8), (3, 128, 4), (3, 160, 4), (3, 160, 8)]
+    out = []
+    for d, N, T in cases:
+        fp = lsg.footprint_bytes(d, N, T, N + 2, precision)
+        row = dict(d=d, N=N, T=T, footprint_gb=fp / 2 ** 30)
+        if fp > (budget_gb << 30):
+            srv = lsg.Server(budget_gb << 30, max_inflight=1)
+            one = np.ones(1)
+            nq = (N + 2) ** d
+            z = np.ones(nq)
+            row["submit_status"] = srv.submit(0, d, N, T, z, z, z, precision=precision)
+            srv.close()
+            out.append(row)
+            continue
+        p = W.random_exp_problem(d, N, T, 777 + N, 778 + N, 779 + N, sigma=0.5)
+        data = [(dict(d=d, N=N, T=T, arrival_unit=0.0), p)]
+        r = _serve_once(lsg, W, data, 0.0, precision, budget_gb << 30, 1, world)
+        row.update(status="ok" if r["completed"] else ("ilu_breakdown" if r["ilu_breakdown"] else "error"),
+                   latency_ms=r.get("p50_ms"), wall_s=r["wall_s"])
+        out.append(row)
+    return out
+
+
+def run_c3(lsg, W, torch, dev, world):
+    """Config 3 (3D N=128): FP64 PCG to 1e-12 against the mixed form (TF32 and BF16 tensor-core
+    products, FP32 ILU(0), FP64 refinement to 1e-10).  With the configuration's T = 6 the ILU(0)
+    of M does not exist (non-positive pivots); the comparison runs on its stand-in with the same
+    seeds (11-13) and series and truncation of degree 4, where it exists.  Each result states its
+    true relative residual from the library's FP64 K x (which the tests pin to the oracle's at
+    1e-11; the full-size test also checks these solves with the oracle's own K x)."""
+    out = {}
+    pc = W.exp_3d()
+    c = lsg.Context(3, pc["N"], pc["T"], torch.tensor(pc["a"], device=dev), torch.tensor(pc["b"], device=dev),
+                    precision=lsg.MIXED_TF32, allow_breakdown=True)
+    out["t6_ilu_status"] = c.status
+    c.close()
+    p = W.random_exp_problem(3, 128, 4, 11, 12, 13)
+    a, b, f = (torch.tensor(p[k], device=dev) for k in ("a", "b", "f"))
+    sols = {}
+    for name, prec, rtol in (("fp64", lsg.FP64, 1e-12), ("mixed_tf32", lsg.MIXED_TF32, 1e-10),
+                             ("mixed_bf16", lsg.MIXED_BF16, 1e-10)):
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        ctx = lsg.Context(3, 128, 4, a, b, precision=prec, profile=True)
+        F = ctx.load_vector(f)
+        u, info = ctx.pcg_solve(F, rtol=rtol, check=False)
+        s1.record()
+        torch.cuda.synchronize()
+        ms = s0.elapsed_time(s1)
+        sols[name] = u.cpu().numpy()
+        out[name] = dict(solves_s=1e3 / ms, ms_per_solve=ms, status=info["status"], iters=info["iters"],
+                         refinements=info["outer_iters"], relres_true_fp64=info["relres_true"],
+                         setup_ms=dict(assemble=ctx.query(lsg.Q_ASSEMBLE_US) / 1e3, ilu=ctx.query(lsg.Q_ILU_US) / 1e3),
+                         sweeps_ms=(ctx.query(lsg.Q_SWEEP_L_US) + ctx.query(lsg.Q_SWEEP_U_US)) / 1e3,
+                         sweep_launches=ctx.query(lsg.Q_SWEEP_L_CALLS) + ctx.query(lsg.Q_SWEEP_U_CALLS),
+                         kx_ms=(ctx.query(lsg.Q_KX_US) + ctx.query(lsg.Q_KX_LO_US)) / 1e3,
+                         device_gb=ctx.query(lsg.Q_DEVICE_BYTES) / 2 ** 30)
+        ctx.close()
+    x64 = sols["fp64"]
+    for name in ("mixed_tf32", "mixed_bf16"):
+        out[name]["rel_err_vs_fp64_gpu"] = float(np.linalg.norm(sols[name] - x64) / np.linalg.norm(x64))
+    out["workload"] = ("3D N=128 (2,048,383 unknowns), Q=130, seeds 11-13; T=6 (the configuration): ILU(0) "
+                       "breaks down; compared at T=4 with degree-4 series")
     return out
 
 
@@ -475,8 +585,15 @@ def run_native(args, world, rank, local):
     batched = None if args.no_batch else dict(
         fp64=run_batched(lsg, W, torch, dev, world),
         mixed_tf32=run_batched(lsg, W, torch, dev, world, precision=lsg.MIXED_TF32))
-    serving = None if args.no_serving else dict(mixed_tf32=run_serving(lsg, W, world, precision=lsg.MIXED_TF32),
-                                                 fp64=run_serving(lsg, W, world, precision=lsg.FP64))
+    serving = None
+    if not args.no_serving:
+        mixed_srv = run_serving(lsg, W, world, lsg.MIXED_TF32)
+        # plain FP64 on the same requests: its own capacity, and the mixed form's 0.5 mu load
+        fp64_srv = run_serving(lsg, W, world, lsg.FP64, fracs=(),
+                               rates={"mixed_0.50mu": 0.5 * mixed_srv["capacity_mu"]})
+        serving = dict(mixed_tf32=mixed_srv, fp64=fp64_srv,
+                       large_mixed_tf32=run_serving_large(lsg, W, world, lsg.MIXED_TF32))
+    c3 = None if args.no_c3 else run_c3(lsg, W, torch, dev, world)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -500,7 +617,7 @@ def run_native(args, world, rank, local):
                         parallelism=f"replicas x{world}"),
             kx_gdof_s=n / (t_kx * 1e-3) / 1e9, kx_ms=t_kx, minv_ms=t_minv, pcg_iters=iters,
             relres_true=info["relres_true"], breakdown_ms_per_solve=per_solve, mixed=mixed or None,
-            batched=batched, serving=serving,
+            batched=batched, serving=serving, config3=c3,
             roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clocks)
         print(json.dumps(line), flush=True)
 
@@ -534,6 +651,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-c3", action="store_true", help="skip the 3D N=128 FP64-vs-mixed line")
     ap.add_argument("--profile-case", choices=["n256-fp64", "n256-tf32", "n256-bf16"], default=None,
                     help="run one 2D N=256 T=8 setup + solve and exit (the small case of the ncu captures)")
     args = ap.parse_args()

@@ -1440,6 +1440,22 @@ static int launch_fill(AT *out, long long n, unsigned *counter, const int *done,
     return LSG_OK;
 }
 
+// CTAs a sweep needs (lines per CTA: B).  In 1D and 2D the wavefront keeps
+// about n1 / (w+1) lines busy at a time: line v may finish position q once line
+// v-1 has finished q+w, so a line starts w+1 positions after the previous one
+// and takes n1 positions plus a hand-off.  A CTA that finishes its line claims the
+// next free one, so that many CTAs (and a margin) keep the sweep at full speed;
+// more would only wait, holding SMs that other solves running at the same time
+// (batched and served problems) can use.  In 3D the planes are pipelined as
+// well and every SM finds work.
+static long long wavefront_ctas(const Geom &g, int B)
+{
+    const long long bands = (g.nlines + B - 1) / B;
+    if (g.d == 3) return bands;
+    const long long busy = (g.n1 + 16 + g.w) / (g.w + 1) + 2;
+    return std::min(bands, (busy + B - 1) / B + 1);
+}
+
 // Both sweeps with the line-parallel kernel (1D and 2D).
 template <typename V, typename AT>
 static int sweeps_line(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done, cudaStream_t s, int D, size_t smf,
@@ -1459,7 +1475,7 @@ static int sweeps_line(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done
     int dev = 0, nsm = 0;
     LSG_CK(cudaGetDevice(&dev));
     LSG_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const unsigned grid = (unsigned)std::min<long long>(g.nlines, nsm);
+    const unsigned grid = (unsigned)std::min<long long>(wavefront_ctas(g, 1), nsm);
     int slot;
     // forward: L y = r
     A.F = c->Lv;
@@ -1518,8 +1534,7 @@ static int sweeps(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done, cud
     int dev = 0, nsm = 0;
     LSG_CK(cudaGetDevice(&dev));
     LSG_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    long long nbands = (g.nlines + B - 1) / B;
-    unsigned grid = (unsigned)std::min<long long>(nbands, nsm);
+    unsigned grid = (unsigned)std::min<long long>(wavefront_ctas(g, B), nsm);
     LSG_CK(cudaMemsetAsync(c->prog, 0, sizeof(unsigned) * 2 * (size_t)g.nlines, s));
     LSG_CK(cudaMemsetAsync(c->counters + 1, 0, sizeof(unsigned) * 2, s));
     // forward: L y = r

@@ -93,3 +93,21 @@ def test_c3_standin_mixed_true_residual(lsg):
     F = Fd.cpu().numpy()
     assert _true_relres(p, u.cpu().numpy(), F) <= 1e-10
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["FP64", "MIXED_TF32"])
+def test_c3_standin_full_size_true_residual(lsg, prec):
+    """The 3D N=128 stand-in at full size (T=4, degree-4 series, seeds 11-13; 36 GB of FP64
+    factors): FP64 PCG to 1e-12 and the mixed form to 1e-10, each checked with the oracle's
+    matrix-free K x (the oracle's M would not fit the host)."""
+    p = W.random_exp_problem(3, 128, 4, 11, 12, 13)
+    P = getattr(lsg, prec)
+    ctx = lsg.Context(3, 128, 4, torch.tensor(p["a"], device=DEV), torch.tensor(p["b"], device=DEV), precision=P)
+    Fd = ctx.load_vector(torch.tensor(p["f"], device=DEV))
+    rtol = 1e-12 if P == lsg.FP64 else 1e-10
+    u, info = ctx.pcg_solve(Fd, rtol=rtol)
+    assert info["status"] == 0
+    F = Fd.cpu().numpy()
+    assert _true_relres(p, u.cpu().numpy(), F) <= (2e-12 if P == lsg.FP64 else 1e-10)
+    ctx.close()
+
