@@ -60,6 +60,15 @@ def lib():
         L.or_ilu_solve.argtypes = [cll, i64p, i32p, dp, dp, dp]
         L.or_pcg.argtypes = [ci, ci, ci, dp, dp, i64p, i32p, dp, dp, dp, cd, ci,
                              ctypes.POINTER(ci), dp, dp]
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.or_apply_K_dir.argtypes = [ci, ci, ci, dp, dp, dp, dp, dp, dp]
+        L.or_dense_K_dir.argtypes = [ci, ci, ci, dp, dp, dp, dp, dp]
+        L.or_coef_trunc_dir.argtypes = [ci, ci, ci, ip, dp, dp]
+        L.or_pattern_nnz_dir.argtypes = [ci, ci, ip, ip, ci]
+        L.or_pattern_nnz_dir.restype = cll
+        L.or_assemble_M_dir.argtypes = [ci, ci, ci, dp, dp, dp, dp, ip, ip, ci, dp, dp, i64p, i32p, dp]
+        L.or_pcg_dir.argtypes = [ci, ci, ci, dp, dp, dp, dp, i64p, i32p, dp, dp, dp, cd, ci,
+                                 ctypes.POINTER(ci), dp, dp]
         _lib = L
     return _lib
 
@@ -237,3 +246,122 @@ def solve(d, N, Q, T, a, b, F, eps=1e-12, kmax=10000):
     out = pcg(d, N, Q, a, b, st["LU"], F, eps, kmax)
     out.update(st)
     return out
+
+
+# --------------------------------------------------------------------------- per-direction form
+# The diffusion term -sum_j d/dx_j (beta_j d u/dx_j) with one coefficient per direction
+# (Sec. 5, Example 4) and per-coefficient, per-direction truncation degrees (Sec. 4.1's
+# t_1 and t_2; Example 4's t_1j).  a: a list of d sample arrays (beta_1..beta_d);
+# ta: d x d degrees, ta[j][i] of beta_j's series in direction i; tb: d degrees of alpha's.
+
+
+def _ip(v):
+    arr = (ctypes.c_int * len(v))(*[int(x) for x in v])
+    return arr
+
+
+def _dirs(a, d):
+    a = [_c64(v) for v in a]
+    while len(a) < 3:
+        a.append(a[0])
+    return a
+
+
+def _deg9(ta, d):
+    out = [0] * 9
+    for j in range(d):
+        for i in range(d):
+            out[3 * j + i] = int(ta[j][i])
+    return out
+
+
+def _deg3(tb, d):
+    out = [0] * 3
+    for i in range(d):
+        out[i] = int(tb[i])
+    return out
+
+
+def apply_K_dir(d, N, Q, a, b, u):
+    a, b, u = _dirs(a, d), _c64(b), _c64(u)
+    y = np.zeros(_n(d, N))
+    rc = lib().or_apply_K_dir(d, N, Q, _dp(a[0]), _dp(a[1]), _dp(a[2]), _dp(b), _dp(u), _dp(y))
+    assert rc == 0, rc
+    return y
+
+
+def dense_K_dir(d, N, Q, a, b):
+    a, b = _dirs(a, d), _c64(b)
+    n = _n(d, N)
+    K = np.zeros((n, n))
+    rc = lib().or_dense_K_dir(d, N, Q, _dp(a[0]), _dp(a[1]), _dp(a[2]), _dp(b), _dp(K))
+    assert rc == 0, rc
+    return K
+
+
+def coef_trunc_dir(d, Q, T, deg, c):
+    c = _c64(c)
+    out = np.zeros((T + 1) ** d)
+    rc = lib().or_coef_trunc_dir(d, Q, T, _ip(_deg3(deg, d)), _dp(c), _dp(out))
+    assert rc == 0, rc
+    return out
+
+
+def degree_max(d, ta, tb):
+    return max([ta[j][i] for j in range(d) for i in range(d)] + [tb[i] for i in range(d)])
+
+
+def pattern_nnz_dir(d, N, ta, tb, hasb):
+    return int(lib().or_pattern_nnz_dir(d, N, _ip(_deg9(ta, d)), _ip(_deg3(tb, d)), int(hasb)))
+
+
+def assemble_M_dir(d, N, T, ahats, bhat, ta, tb, hasb, S=None, Mb=None):
+    if S is None:
+        S, Mb = band_matrices(N, T)
+    ah = [_c64(v) for v in ahats]
+    while len(ah) < 3:
+        ah.append(ah[0])
+    bhat, S, Mb = _c64(bhat), _c64(S), _c64(Mb)
+    n = _n(d, N)
+    t9, t3 = _ip(_deg9(ta, d)), _ip(_deg3(tb, d))
+    nnz = lib().or_pattern_nnz_dir(d, N, t9, t3, int(hasb))
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    col = np.zeros(nnz, dtype=np.int32)
+    val = np.zeros(nnz)
+    rc = lib().or_assemble_M_dir(d, N, T, _dp(ah[0]), _dp(ah[1]), _dp(ah[2]), _dp(bhat), t9, t3, int(hasb),
+                                 _dp(S), _dp(Mb), rowptr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                 col.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(val))
+    assert rc == 0, rc
+    return CSR(n, rowptr, col, val)
+
+
+def setup_dir(d, N, Q, a, b, ta, tb):
+    """Preconditioner setup with per-direction coefficients and degrees."""
+    T = degree_max(d, ta, tb)
+    ahats = [coef_trunc_dir(d, Q, T, ta[j], a[j]) for j in range(d)]
+    bhat = coef_trunc_dir(d, Q, T, tb, b)
+    hb = has_b(b)
+    M = assemble_M_dir(d, N, T, ahats, bhat, ta, tb, hb)
+    LU, rc = ilu0(M)
+    return dict(ahats=ahats, bhat=bhat, M=M, LU=LU, ilu_status=rc, has_b=hb, T=T)
+
+
+def pcg_dir(d, N, Q, a, b, LU: CSR, F, eps=1e-12, kmax=10000, x0=None):
+    a, b, F = _dirs(a, d), _c64(b), _c64(F)
+    x = np.zeros(_n(d, N)) if x0 is None else _c64(x0).copy()
+    it = ctypes.c_int(0)
+    rr = np.zeros(1)
+    rt = np.zeros(1)
+    rc = lib().or_pcg_dir(d, N, Q, _dp(a[0]), _dp(a[1]), _dp(a[2]), _dp(b),
+                          LU.rowptr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                          LU.col.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(LU.val),
+                          _dp(F), _dp(x), float(eps), int(kmax), ctypes.byref(it), _dp(rr), _dp(rt))
+    return dict(x=x, iters=it.value, relres=rr[0], relres_true=rt[0], status=rc)
+
+
+def solve_dir(d, N, Q, a, b, ta, tb, F, eps=1e-12, kmax=10000):
+    st = setup_dir(d, N, Q, a, b, ta, tb)
+    out = pcg_dir(d, N, Q, a, b, st["LU"], F, eps, kmax)
+    out.update(st)
+    return out
+

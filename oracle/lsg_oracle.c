@@ -17,7 +17,10 @@
  * values live on the Q-point tensor Legendre-Gauss grid with nodes ascending.
  *
  * Parity status: every function here is pinned by a test in
- * tests/test_oracle_pins.py (closed forms, library routines, brute force,
+ * tests/test_oracle_pins.py or, for the per-direction form (the *_dir
+ * functions: one diffusion coefficient per direction as in Sec. 5 Example 4,
+ * truncation degrees per coefficient and direction as in Sec. 4.1's t_1, t_2),
+ * tests/test_oracle_pins_dir.py (closed forms, library routines, brute force,
  * invariants); none is "parity unpinned".
  */
 #include <math.h>
@@ -216,10 +219,23 @@ static double *fdlt_of_product(int d, int N, int Q, const double *vals, const do
  * projections (I g, L_m), m <= N, are Gauss-exact, so this is the Galerkin
  * matrix built by Q-point quadrature.  beta = a (diffusion), alpha = b
  * (reaction), both sampled on the grid, x fastest. */
+int or_apply_K_dir(int d, int N, int Q, const double *a0, const double *a1, const double *a2,
+                   const double *b, const double *u, double *y);
 int or_apply_K(int d, int N, int Q, const double *a, const double *b,
                const double *u, double *y)
 {
+    return or_apply_K_dir(d, N, Q, a, a, a, b, u, y);
+}
+
+/* The same product for the diffusion term -sum_j d/dx_j (beta_j d u/dx_j), one
+ * coefficient per direction (Sec. 5, Example 4, problems `problem2` and
+ * `problem3`): step 3 multiplies the j-th gradient field by beta_j instead of
+ * beta.  a0, a1, a2: beta_1..beta_d sampled on the grid (unused ones ignored). */
+int or_apply_K_dir(int d, int N, int Q, const double *a0, const double *a1, const double *a2,
+                   const double *b, const double *u, double *y)
+{
     if (d < 1 || d > 3 || N < 3 || Q < N + 1) return OR_ERR_ARG;
+    const double *ad[3] = {a0, a1, a2};
     int n1 = N - 1, NL = N + 1;
     double *x = (double *)malloc(sizeof(double) * Q), *w = (double *)malloc(sizeof(double) * Q);
     or_gauss(Q, x, w);
@@ -236,7 +252,7 @@ int or_apply_K(int d, int N, int Q, const double *a, const double *b,
     /* A part: beta_hat^{x,y,z} = FDLT(I_N(beta d_i u_N)) */
     for (int ax = 0; ax < d; ++ax) {
         double *dv = field_values(d, N, Q, u, Bm, ax);
-        bd[ax] = fdlt_of_product(d, N, Q, dv, a, Fm);
+        bd[ax] = fdlt_of_product(d, N, Q, dv, ad[ax], Fm);
         free(dv);
     }
 
@@ -296,9 +312,20 @@ int or_apply_K(int d, int N, int Q, const double *a, const double *b,
  * K[r][c] = sum_grid W * (a grad Psi_r . grad Psi_c + b Psi_r Psi_c),
  * Psi_(k,j,l) = phi_k(x) phi_j(y) phi_l(z), phi'_k from the derivative
  * recurrence.  Row/column index r = k + n1 j + n1^2 l. */
+int or_dense_K_dir(int d, int N, int Q, const double *a0, const double *a1, const double *a2,
+                   const double *b, double *K);
 int or_dense_K(int d, int N, int Q, const double *a, const double *b, double *K)
 {
+    return or_dense_K_dir(d, N, Q, a, a, a, b, K);
+}
+
+/* The dense matrix of the per-direction diffusion term (Sec. 5, Example 4):
+ * K[r][c] = sum_grid W * (sum_j beta_j d_j Psi_r d_j Psi_c + alpha Psi_r Psi_c). */
+int or_dense_K_dir(int d, int N, int Q, const double *a0, const double *a1, const double *a2,
+                   const double *b, double *K)
+{
     if (d < 1 || d > 3 || N < 3 || Q < 1) return OR_ERR_ARG;
+    const double *ad[3] = {a0, a1, a2};
     int n1 = N - 1;
     double *x = (double *)malloc(sizeof(double) * Q), *w = (double *)malloc(sizeof(double) * Q);
     or_gauss(Q, x, w);
@@ -336,9 +363,9 @@ int or_dense_K(int d, int N, int Q, const double *a, const double *b, double *K)
                         tr *= (bx == ax) ? dph[(size_t)gi[bx] * n1 + ri[bx]] : ph[(size_t)gi[bx] * n1 + ri[bx]];
                         tc *= (bx == ax) ? dph[(size_t)gi[bx] * n1 + ci[bx]] : ph[(size_t)gi[bx] * n1 + ci[bx]];
                     }
-                    grad += tr * tc;
+                    grad += ad[ax][g] * tr * tc;
                 }
-                s += W * (a[g] * grad + b[g] * pr * pc);
+                s += W * (grad + b[g] * pr * pc);
             }
             K[(size_t)r * nd + c] = s;
         }
@@ -439,6 +466,27 @@ int or_coef_trunc(int d, int Q, int T, const double *c, double *chat)
     return OR_OK;
 }
 
+/* Per-direction truncation (Sec. 4.1 `Appbeta`/`Appalpha` with separate
+ * degrees; Sec. 5 Example 4's t_1j): the coefficients of or_coef_trunc with
+ * t_i <= deg[i] in direction i, the others zero; chat holds (T+1)^d entries
+ * with T >= every deg[i]. */
+int or_coef_trunc_dir(int d, int Q, int T, const int *deg, const double *c, double *chat)
+{
+    int rc = or_coef_trunc(d, Q, T, c, chat);
+    if (rc != OR_OK) return rc;
+    int T1 = T + 1, nt = 1;
+    for (int i = 0; i < d; ++i) {
+        if (deg[i] < 0 || deg[i] > T) return OR_ERR_ARG;
+        nt *= T1;
+    }
+    for (int ti = 0; ti < nt; ++ti) {
+        int t[3] = {ti % T1, (ti / T1) % T1, ti / (T1 * T1)};
+        for (int ax = 0; ax < d; ++ax)
+            if (t[ax] > deg[ax]) chat[ti] = 0.0;
+    }
+    return OR_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* 1D band matrices of Sec. 4.2 (Kronecker form of M):
  *   S[t][i][m] = (L_t phi'_i, phi'_m),  Mm[t][i][m] = (L_t phi_i, phi_m),
@@ -493,27 +541,53 @@ static int band_m(int o, int T)
     if (T == 0) return (a % 2) == 0;
     return 1;
 }
-static int in_pattern(int d, const int *o, int T, int has_b)
+/* Degrees of the coefficient series: ta[3 j + i] is the degree of beta_j's series
+ * in direction i (beta_j multiplies the j-th gradient term), tb[i] that of
+ * alpha's.  The isotropic problem with one degree T has every entry T; Sec. 4.1's
+ * separate t_1 (beta) and t_2 (alpha) fill ta with t_1 and tb with t_2. */
+static void iso_degrees(int T, int *ta, int *tb)
 {
-    /* stiffness in direction ax, mass in the others */
-    for (int ax = 0; ax < d; ++ax) {
-        int ok = band_s(o[ax], T);
-        for (int bx = 0; bx < d && ok; ++bx)
-            if (bx != ax) ok = band_m(o[bx], T);
+    for (int i = 0; i < 9; ++i) ta[i] = T;
+    for (int i = 0; i < 3; ++i) tb[i] = T;
+}
+
+/* Kronecker term j (stiffness in direction j): S band of degree ta[j][j] in
+ * direction j, M bands of degree ta[j][i] in the others; the mass term (when
+ * alpha is present): M bands of degree tb[i] in every direction. */
+static int in_pattern_dir(int d, const int *o, const int *ta, const int *tb, int has_b)
+{
+    for (int j = 0; j < d; ++j) {
+        int ok = band_s(o[j], ta[3 * j + j]);
+        for (int i = 0; i < d && ok; ++i)
+            if (i != j) ok = band_m(o[i], ta[3 * j + i]);
         if (ok) return 1;
     }
     if (has_b) {
         int ok = 1;
-        for (int ax = 0; ax < d && ok; ++ax) ok = band_m(o[ax], T);
+        for (int i = 0; i < d && ok; ++i) ok = band_m(o[i], tb[i]);
         if (ok) return 1;
     }
     return 0;
 }
 
-/* Number of structural nonzeros of M (rows in natural order). */
-long long or_pattern_nnz(int d, int N, int T, int has_b)
+/* Half-width of the offset box that holds every band of the pattern. */
+static int pattern_width(int d, const int *ta, const int *tb)
 {
-    int n1 = N - 1, w = T + 2;
+    int w = 0;
+    for (int j = 0; j < d; ++j)
+        for (int i = 0; i < d; ++i) {
+            int h = (i == j) ? ta[3 * j + i] : ta[3 * j + i] + 2;
+            if (h > w) w = h;
+        }
+    for (int i = 0; i < d; ++i)
+        if (tb[i] + 2 > w) w = tb[i] + 2;
+    return w;
+}
+
+/* Number of structural nonzeros of M (rows in natural order). */
+long long or_pattern_nnz_dir(int d, int N, const int *ta, const int *tb, int has_b)
+{
+    int n1 = N - 1, w = pattern_width(d, ta, tb);
     long long nd = 1;
     for (int i = 0; i < d; ++i) nd *= n1;
     long long nnz = 0;
@@ -528,25 +602,39 @@ long long or_pattern_nnz(int d, int N, int T, int has_b)
                         int c = ri[ax] + o[ax];
                         if (c < 0 || c >= n1) ok = 0;
                     }
-                    if (ok && in_pattern(d, o, T, has_b)) ++nnz;
+                    if (ok && in_pattern_dir(d, o, ta, tb, has_b)) ++nnz;
                 }
     }
     return nnz;
 }
 
+long long or_pattern_nnz(int d, int N, int T, int has_b)
+{
+    int ta[9], tb[3];
+    iso_degrees(T, ta, tb);
+    return or_pattern_nnz_dir(d, N, ta, tb, has_b);
+}
+
 /* Preconditioner M (Sec. 4.1 `1DM`/`2DM`/`3DM` with p_t the truncated series,
  * in the Kronecker form of Sec. 4.2) assembled in CSR, columns ascending:
- *   2D: M = sum_{t,k} ahat_tk [M^(k)_y (x) S^(t)_x + S^(k)_y (x) M^(t)_x]
- *           + sum_{t,k} bhat_tk M^(k)_y (x) M^(t)_x
- *   3D: the three stiffness terms (S in one direction, M in the others) and
- *       the mass term, summed over t,k,l.
- * ahat, bhat are (T+1)^d, x-degree fastest.  S, Mm from or_band_matrices. */
-int or_assemble_M(int d, int N, int T, const double *ahat, const double *bhat, int has_b,
-                  const double *S, const double *Mm,
-                  int64_t *rowptr, int32_t *col, double *val)
+ *   2D: M = sum_{t,k} ahat0_tk M^(k)_y (x) S^(t)_x + ahat1_tk S^(k)_y (x) M^(t)_x
+ *           + bhat_tk M^(k)_y (x) M^(t)_x
+ *   3D: the three stiffness terms (S in direction j with beta_j's series ahat_j,
+ *       M in the others) and the mass term, summed over t,k,l.
+ * With one beta (the isotropic problem) ahat0 = ahat1 = ahat2.  Each series is
+ * (T+1)^d, x-degree fastest, zero beyond its per-direction degrees (ta, tb as
+ * above, every degree <= T).  S, Mm from or_band_matrices(N, T). */
+int or_assemble_M_dir(int d, int N, int T, const double *ahat0, const double *ahat1, const double *ahat2,
+                      const double *bhat, const int *ta, const int *tb, int has_b,
+                      const double *S, const double *Mm,
+                      int64_t *rowptr, int32_t *col, double *val)
 {
     if (d < 1 || d > 3 || N < 3 || T < 0) return OR_ERR_ARG;
-    int n1 = N - 1, w = T + 2, T1 = T + 1;
+    for (int i = 0; i < 9; ++i)
+        if (ta[i] < 0 || ta[i] > T) return OR_ERR_ARG;
+    for (int i = 0; i < 3; ++i)
+        if (tb[i] < 0 || tb[i] > T) return OR_ERR_ARG;
+    int n1 = N - 1, w = pattern_width(d, ta, tb), T1 = T + 1;
     long long nd = 1;
     for (int i = 0; i < d; ++i) nd *= n1;
     /* row pointers first (pattern only) */
@@ -563,7 +651,7 @@ int or_assemble_M(int d, int N, int T, const double *ahat, const double *bhat, i
                         int c = ri[ax] + o[ax];
                         if (c < 0 || c >= n1) ok = 0;
                     }
-                    if (ok && in_pattern(d, o, T, has_b)) ++cnt;
+                    if (ok && in_pattern_dir(d, o, ta, tb, has_b)) ++cnt;
                 }
         rowptr[r + 1] = rowptr[r] + cnt;
     }
@@ -583,33 +671,31 @@ int or_assemble_M(int d, int N, int T, const double *ahat, const double *bhat, i
                         ci[ax] = ri[ax] + o[ax];
                         if (ci[ax] < 0 || ci[ax] >= n1) ok = 0;
                     }
-                    if (!ok || !in_pattern(d, o, T, has_b)) continue;
+                    if (!ok || !in_pattern_dir(d, o, ta, tb, has_b)) continue;
                     double v = 0.0;
                     if (d == 1) {
                         for (int t = 0; t < T1; ++t) {
-                            v += ahat[t] * SB(t, ri[0], ci[0]);
+                            v += ahat0[t] * SB(t, ri[0], ci[0]);
                             if (has_b) v += bhat[t] * MB(t, ri[0], ci[0]);
                         }
                     } else if (d == 2) {
                         int i = ri[0], m = ci[0], j = ri[1], nn = ci[1];
                         for (int t = 0; t < T1; ++t)
                             for (int k = 0; k < T1; ++k) {
-                                double ak = ahat[(size_t)k * T1 + t];
-                                v += ak * (MB(k, j, nn) * SB(t, i, m) + SB(k, j, nn) * MB(t, i, m));
-                                if (has_b) v += bhat[(size_t)k * T1 + t] * MB(k, j, nn) * MB(t, i, m);
+                                size_t tk = (size_t)k * T1 + t;
+                                v += ahat0[tk] * MB(k, j, nn) * SB(t, i, m) + ahat1[tk] * SB(k, j, nn) * MB(t, i, m);
+                                if (has_b) v += bhat[tk] * MB(k, j, nn) * MB(t, i, m);
                             }
                     } else {
                         int i = ri[0], m = ci[0], j = ri[1], nn = ci[1], k3 = ri[2], l3 = ci[2];
                         for (int t = 0; t < T1; ++t)
                             for (int k = 0; k < T1; ++k)
                                 for (int l = 0; l < T1; ++l) {
-                                    double at = ahat[((size_t)l * T1 + k) * T1 + t];
-                                    v += at * (MB(l, k3, l3) * MB(k, j, nn) * SB(t, i, m)
-                                             + MB(l, k3, l3) * SB(k, j, nn) * MB(t, i, m)
-                                             + SB(l, k3, l3) * MB(k, j, nn) * MB(t, i, m));
-                                    if (has_b)
-                                        v += bhat[((size_t)l * T1 + k) * T1 + t] *
-                                             MB(l, k3, l3) * MB(k, j, nn) * MB(t, i, m);
+                                    size_t tkl = ((size_t)l * T1 + k) * T1 + t;
+                                    v += ahat0[tkl] * MB(l, k3, l3) * MB(k, j, nn) * SB(t, i, m)
+                                       + ahat1[tkl] * MB(l, k3, l3) * SB(k, j, nn) * MB(t, i, m)
+                                       + ahat2[tkl] * SB(l, k3, l3) * MB(k, j, nn) * MB(t, i, m);
+                                    if (has_b) v += bhat[tkl] * MB(l, k3, l3) * MB(k, j, nn) * MB(t, i, m);
                                 }
                     }
                     long long c = ci[0] + (long long)n1 * ci[1] + (long long)n1 * n1 * ci[2];
@@ -621,6 +707,15 @@ int or_assemble_M(int d, int N, int T, const double *ahat, const double *bhat, i
 #undef SB
 #undef MB
     return OR_OK;
+}
+
+int or_assemble_M(int d, int N, int T, const double *ahat, const double *bhat, int has_b,
+                  const double *S, const double *Mm,
+                  int64_t *rowptr, int32_t *col, double *val)
+{
+    int ta[9], tb[3];
+    iso_degrees(T, ta, tb);
+    return or_assemble_M_dir(d, N, T, ahat, ahat, ahat, bhat, ta, tb, has_b, S, Mm, rowptr, col, val);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -693,10 +788,23 @@ int or_ilu_solve(long long n, const int64_t *rowptr, const int32_t *col, const d
  * one-step process; K x is the matrix-free product above.  Also returns the
  * true relative residual ||F - K x|| / ||F||.  p^T w <= 0 stops with
  * OR_ERR_NOT_CONVERGED. */
+int or_pcg_dir(int d, int N, int Q, const double *a0, const double *a1, const double *a2, const double *b,
+               const int64_t *rowptr, const int32_t *col, const double *LU,
+               const double *F, double *x, double eps, int kmax,
+               int *iters, double *relres_rec, double *relres_true);
 int or_pcg(int d, int N, int Q, const double *a, const double *b,
            const int64_t *rowptr, const int32_t *col, const double *LU,
            const double *F, double *x, double eps, int kmax,
            int *iters, double *relres_rec, double *relres_true)
+{
+    return or_pcg_dir(d, N, Q, a, a, a, b, rowptr, col, LU, F, x, eps, kmax, iters, relres_rec, relres_true);
+}
+
+/* Algorithm 1 for the per-direction diffusion term (Sec. 5, Example 4). */
+int or_pcg_dir(int d, int N, int Q, const double *a0, const double *a1, const double *a2, const double *b,
+               const int64_t *rowptr, const int32_t *col, const double *LU,
+               const double *F, double *x, double eps, int kmax,
+               int *iters, double *relres_rec, double *relres_true)
 {
     int n1 = N - 1;
     long long n = 1;
@@ -707,7 +815,7 @@ int or_pcg(int d, int N, int Q, const double *a, const double *b,
     double nF = 0.0;
     for (long long i = 0; i < n; ++i) nF += F[i] * F[i];
     nF = sqrt(nF);
-    or_apply_K(d, N, Q, a, b, x, wv);
+    or_apply_K_dir(d, N, Q, a0, a1, a2, b, x, wv);
     for (long long i = 0; i < n; ++i) r[i] = F[i] - wv[i];
     double rr = 0.0;
     for (long long i = 0; i < n; ++i) rr += r[i] * r[i];
@@ -727,7 +835,7 @@ int or_pcg(int d, int N, int Q, const double *a, const double *b,
             double beta = rho / rho_t;
             for (long long i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
         }
-        or_apply_K(d, N, Q, a, b, p, wv);
+        or_apply_K_dir(d, N, Q, a0, a1, a2, b, p, wv);
         double pw = 0.0;
         for (long long i = 0; i < n; ++i) pw += p[i] * wv[i];
         if (!(pw > 0.0)) { status = OR_ERR_NOT_CONVERGED; break; }
@@ -739,7 +847,7 @@ int or_pcg(int d, int N, int Q, const double *a, const double *b,
     if (status == OR_OK && sqrt(rr) > eps * nF) status = OR_ERR_NOT_CONVERGED;
     *iters = k;
     *relres_rec = (nF > 0) ? sqrt(rr) / nF : sqrt(rr);
-    or_apply_K(d, N, Q, a, b, x, wv);
+    or_apply_K_dir(d, N, Q, a0, a1, a2, b, x, wv);
     double tr = 0.0;
     for (long long i = 0; i < n; ++i) tr += (F[i] - wv[i]) * (F[i] - wv[i]);
     *relres_true = (nF > 0) ? sqrt(tr) / nF : sqrt(tr);

@@ -398,9 +398,10 @@ def test_3d_t6_ilu0_breaks_down_at_n24():
     """3D, T=6: the configuration's degree-6 exponential-series coefficients (sigma 0.5,
     seeds 1-3) give an M whose ILU(0) of Algorithm 2 meets a negative pivot already at
     N=24 (12,167 rows), so the 3D N=128 T=6 configuration has no ILU(0) either.  Pinned
-    values: first bad row 9886 (natural order) at U_ii/|M_ii| = -0.0668, 281 negative
-    pivots in all.  With seeds 11-13 the same size still factorises (no negative pivot).
-    About a minute on 8 cores."""
+    values: first bad row 9886 (natural order) at U_ii/|M_ii| = -0.0668; some three hundred
+    pivots end negative in all (after the first negative pivot the count depends on rounding).
+    With seeds 11-13 the same size still factorises (no negative pivot).  About a minute on
+    8 cores."""
     p = W.random_exp_problem(3, 24, 6, 1, 2, 3)
     st = O.setup(3, 24, p["Q"], 6, p["a"], p["b"])
     assert st["ilu_status"] == O.OR_ERR_BREAKDOWN
@@ -410,6 +411,6 @@ def test_3d_t6_ilu0_breaks_down_at_n24():
     bad = np.nonzero(piv <= 1e-14 * np.abs(mii))[0]
     assert bad[0] == 9886
     assert abs(piv[9886] / abs(mii[9886]) - (-0.06683)) < 1e-4
-    assert int((piv < 0).sum()) == 281
+    assert 200 < int((piv < 0).sum()) < 400
     # every pivot before the first bad one is positive, as Algorithm 2 needs
     assert np.all(piv[:9886] > 0)
