@@ -85,7 +85,9 @@ enum lsg_export_item {
     LSG_EXPORT_BAND_S = 4,    /* (T+1) x (N-1) x (2w+1): S^(t)[i][i+o] = (L_t phi'_i, phi'_{i+o}), o = -w..w */
     LSG_EXPORT_BAND_M = 5,    /* (T+1) x (N-1) x (2w+1): M^(t)[i][i+o] = (L_t phi_i, phi_{i+o}) */
     LSG_EXPORT_M = 6,         /* n x S stencil of M (needs LSG_SETUP_KEEP_M) */
-    LSG_EXPORT_LU = 7         /* n x S stencil of the ILU(0) factors (L strictly lower, U upper) */
+    LSG_EXPORT_LU = 7,        /* n x S stencil of the ILU(0) factors (L strictly lower, U upper) */
+    LSG_EXPORT_AHAT_Y = 8,    /* truncated series of the y-direction diffusion coefficient (lsg_setup_problem) */
+    LSG_EXPORT_AHAT_Z = 9     /* truncated series of the z-direction diffusion coefficient */
 };
 
 /* lsg_query items */
@@ -169,6 +171,31 @@ int lsg_setup(lsg_ctx **out, int d, int N, int T, int Q, const double *a, const 
               int precision, lsg_stream_t stream);
 int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, const double *b,
                  int precision, unsigned flags, lsg_stream_t stream);
+
+/* The general problem: a diffusion coefficient per direction and truncation
+ * degrees per coefficient and direction,
+ *     -sum_j d/dx_j (a_j(x) du/dx_j) + b(x) u = f,
+ * the form of Sec. 5 Example 4 (`problem2`, `problem3`: beta_1(x), beta_2(y),
+ * beta_3(z)); a_j = a for all j is the problem of lsg_setup.  The preconditioner
+ * replaces each a_j by its Legendre series truncated to degree ta[j][i] in
+ * direction i and b by its series of degrees tb[i] (Sec. 4.1 with separate t_1 for
+ * the diffusion and t_2 for the reaction coefficient; Example 4's t_1j); its
+ * structural pattern is the union of the Kronecker terms' bands for those degrees
+ * (stiffness band of degree ta[j][j] in direction j, mass bands of degree ta[j][i]
+ * in the others; mass bands of degrees tb[i] for b when b is not identically 0).
+ * Sizes as in lsg_setup; degrees 0..64; a[j] for j >= d ignored (NULL there,
+ * or a[j] == a[0], means the same samples). */
+typedef struct {
+    int d, N, Q;          /* Q <= 0 selects Q = N+2 */
+    const double *a[3];   /* Q^d samples of a_1..a_d (host or device, copied) */
+    const double *b;      /* Q^d samples of b */
+    int ta[3][3];         /* ta[j][i]: degree of a_j's series in direction i */
+    int tb[3];            /* tb[i]: degree of b's series in direction i */
+    int precision;        /* lsg_precision */
+    unsigned flags;       /* LSG_SETUP_* */
+} lsg_problem;
+/* Build a context for the general problem (otherwise as lsg_setup_ex). */
+int lsg_setup_problem(lsg_ctx **out, const lsg_problem *p, lsg_stream_t stream);
 
 /* F_k = (f, Psi_k) by Q-point quadrature of the samples f (Q^d, Sec. 3). */
 int lsg_load_vector(lsg_ctx *ctx, const double *f, double *F, lsg_stream_t stream);

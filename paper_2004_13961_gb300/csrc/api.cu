@@ -115,31 +115,33 @@ static size_t footprint(const Geom &g, int precision, unsigned flags)
 
 // Structural nonzeros of M: the pattern is a union of product sets (one per
 // Kronecker term), so count it by inclusion-exclusion over the terms, with the
-// in-grid count of a product set factorising over the axes.
-static long long axis_count(int n1, int T, int kind)  // kind bit0: stiffness band, bit1: mass band
+// in-grid count of a product set factorising over the axes.  On one axis a term
+// is a stiffness band (its own direction) or a mass band of the term's degree
+// there; the offsets counted are those every term of the subset allows.
+static bool band_ok(int o, int kind, int T)  // kind 1: stiffness band, 2: mass band
 {
-    long long cnt = 0;
-    for (int o = -(T + 2); o <= T + 2; ++o) {
-        int a = o < 0 ? -o : o;
-        bool in = true;
-        if (kind & 1) in = in && a <= T;
-        if (kind & 2) in = in && a <= T + 2 && (T > 0 || (a % 2) == 0);
-        if (!in) continue;
-        cnt += std::max(0, n1 - a);
-    }
-    return cnt;
+    const int a = o < 0 ? -o : o;
+    if (kind == 1) return a <= T;
+    return a <= T + 2 && (T > 0 || (a % 2) == 0);
 }
 long long structural_nnz(const Geom &g)
 {
-    int nt = g.d + (g.has_b ? 1 : 0);
+    const int nt = g.d + (g.has_b ? 1 : 0);  // terms: d stiffness terms, then the mass term
     long long total = 0;
     for (int mask = 1; mask < (1 << nt); ++mask) {
         long long prod = 1;
         for (int ax = 0; ax < g.d; ++ax) {
-            int kind = 0;
-            for (int t = 0; t < nt; ++t)
-                if (mask & (1 << t)) kind |= (t == ax) ? 1 : 2;
-            prod *= axis_count(g.n1, g.T, kind);
+            long long cnt = 0;
+            for (int o = -g.w; o <= g.w; ++o) {
+                bool in = true;
+                for (int t = 0; t < nt && in; ++t) {
+                    if (!(mask & (1 << t))) continue;
+                    if (t < g.d) in = band_ok(o, t == ax ? 1 : 2, g.ta[t][ax]);
+                    else in = band_ok(o, 2, g.tb[ax]);
+                }
+                if (in) cnt += std::max(0, g.n1 - (o < 0 ? -o : o));
+            }
+            prod *= cnt;
         }
         total += (__builtin_popcount(mask) & 1) ? prod : -prod;
     }
@@ -199,9 +201,14 @@ static void free_ctx(lsg_ctx *c, cudaStream_t s)
     void *ptrs[] = {c->gx, c->gw, c->tab, c->Wa, c->Wb, c->Wg, c->ahat, c->bhat, c->bandS, c->bandM,
                     c->Lv, c->Uv, c->Mkeep, c->order, c->rowflag, c->prog, c->counters, c->err, c->ws, c->ws32,
                     c->r, c->z, c->p, c->wv, c->xs, c->fs, c->ys, c->red, c->st, c->r32, c->z32, c->p32, c->w32,
-                    c->e32, c->e64, c->u64, c->y32, c->Wa32, c->Wb32, c->tct};
-    for (void *p : ptrs)
-        if (p) cudaFreeAsync(p, s);
+                    c->e32, c->e64, c->u64, c->y32, c->Wa32, c->Wb32, c->tct,
+                    c->Way, c->Waz, c->Wa32y, c->Wa32z, c->ahaty, c->ahatz};
+    const int np = (int)(sizeof ptrs / sizeof ptrs[0]);
+    for (int i = 0; i < np; ++i) {
+        bool dup = false;  // per-direction arrays may alias the first direction's
+        for (int k = 0; k < i && !dup; ++k) dup = ptrs[k] == ptrs[i];
+        if (ptrs[i] && !dup) cudaFreeAsync(ptrs[i], s);
+    }
     cudaStreamSynchronize(s);
     cudaGetLastError();
     release_pinned_state(c->st_host);
@@ -291,18 +298,29 @@ size_t lsg_footprint_bytes(int d, int N, int T, int Q, int precision)
     return footprint(make_geom(d, N, T, Q), precision, 0);
 }
 
-int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, const double *b, int precision,
-                 unsigned flags, lsg_stream_t stream)
+// Setup for one diffusion coefficient per direction (a[j] multiplies the j-th
+// gradient term; a[j] == a[0] for the scalar coefficient) with truncation degrees
+// per coefficient and direction.
+static int setup_impl(lsg_ctx **out, int d, int N, const int ta[3][3], const int tb[3], int Q,
+                      const double *const *a, const double *b, int precision, unsigned flags, cudaStream_t s)
 {
-    if (!out || !a || !b) return LSG_ERR_ARG;
+    if (!out || !b) return LSG_ERR_ARG;
     *out = nullptr;
+    if (d < 1 || d > 3) return LSG_ERR_ARG;
+    for (int j = 0; j < d; ++j) {
+        if (!a[j]) return LSG_ERR_ARG;
+        if (tb[j] < 0 || tb[j] > 64) return LSG_ERR_ARG;
+        for (int i = 0; i < d; ++i)
+            if (ta[j][i] < 0 || ta[j][i] > 64) return LSG_ERR_ARG;
+    }
     if (Q <= 0) Q = N + 2;
-    LSG_TRY(check_sizes(d, N, T, Q));
+    const Geom g0 = make_geom_dir(d, N, ta, tb, Q);
+    LSG_TRY(check_sizes(d, N, g0.T, Q));
+    if (g0.w > 66) return LSG_ERR_ARG;
     if (precision < LSG_FP64 || precision > LSG_MIXED_BF16) return LSG_ERR_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
     lsg_ctx *c = new lsg_ctx{};
     c->stream = s;
-    c->g = make_geom(d, N, T, Q);
+    c->g = g0;
     c->precision = precision;
     c->flags = flags;
     c->wait_budget = kSpinBudgetCycles;
@@ -333,6 +351,31 @@ int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, con
     ALLOC(c->Wg, z.grid);
     ALLOC(c->ahat, z.series);
     ALLOC(c->bhat, z.series);
+    // the other directions' coefficients: separate arrays only where the samples (or,
+    // for the series, the degrees) differ from a direction already held
+    auto same_deg = [&](int j, int k) {
+        for (int i = 0; i < 3; ++i)
+            if (g.ta[j][i] != g.ta[k][i]) return false;
+        return true;
+    };
+    c->Way = c->Waz = c->Wa;
+    c->ahaty = c->ahatz = c->ahat;
+    if (d >= 2) {
+        c->own_ay = a[1] != a[0];
+        if (c->own_ay) ALLOC(c->Way, z.grid);
+        if (!(a[1] == a[0] && same_deg(1, 0))) ALLOC(c->ahaty, z.series);
+    }
+    if (d == 3) {
+        if (a[2] == a[0]) c->Waz = c->Wa;
+        else if (a[2] == a[1]) c->Waz = c->Way;
+        else {
+            c->own_az = 1;
+            ALLOC(c->Waz, z.grid);
+        }
+        if (a[2] == a[0] && same_deg(2, 0)) c->ahatz = c->ahat;
+        else if (a[2] == a[1] && same_deg(2, 1)) c->ahatz = c->ahaty;
+        else ALLOC(c->ahatz, z.series);
+    }
     ALLOC(c->bandS, z.band);
     ALLOC(c->bandM, z.band);
     ALLOC(c->Lv, z.Lv);
@@ -362,39 +405,54 @@ int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, con
         ALLOC(c->y32, (size_t)g.n * 4);
         ALLOC(c->Wa32, (size_t)g.nq * 4);
         ALLOC(c->Wb32, (size_t)g.nq * 4);
+        c->Wa32y = c->Wa32z = c->Wa32;
+        if (c->own_ay) ALLOC(c->Wa32y, (size_t)g.nq * 4);
+        if (c->own_az) ALLOC(c->Wa32z, (size_t)g.nq * 4);
+        else if (d == 3 && c->Waz == c->Way) c->Wa32z = c->Wa32y;
         ALLOC(c->e64, z.vec);
         ALLOC(c->u64, z.vec);
         ALLOC(c->ws32, z.ws / 2);
         ALLOC(c->tct, tc_table_bytes(g, precision));
     }
-    double *sa = nullptr, *sb = nullptr;
-    bool ha = !is_device_ptr(a), hb = !is_device_ptr(b);
-    if (ha) ALLOC(sa, z.grid);
-    if (hb) ALLOC(sb, z.grid);
+    // host samples are staged in temporary device arrays (one per distinct array)
+    double *stage[4] = {nullptr, nullptr, nullptr, nullptr};
+    const double *dev_in[4] = {a[0], d >= 2 ? a[1] : a[0], d == 3 ? a[2] : a[0], b};
+    const double *host_in[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0; k < 4; ++k) {
+        if (is_device_ptr(dev_in[k])) continue;
+        int same = -1;
+        for (int m = 0; m < k && same < 0; ++m)
+            if (host_in[m] == dev_in[k]) same = m;
+        host_in[k] = dev_in[k];
+        if (same >= 0) {
+            stage[k] = nullptr;
+            dev_in[k] = stage[same];
+            continue;
+        }
+        ALLOC(stage[k], z.grid);
+        dev_in[k] = stage[k];
+    }
 #undef ALLOC
     if (st == LSG_OK && !(c->st_host = pinned_state())) st = LSG_ERR_NOMEM;
+    auto release_stage = [&]() {
+        for (int k = 0; k < 4; ++k)
+            if (stage[k]) cudaFreeAsync(stage[k], s);
+        for (int k = 0; k < 4; ++k) stage[k] = nullptr;
+    };
     if (st != LSG_OK) {
-        if (sa) cudaFreeAsync(sa, s);
-        if (sb) cudaFreeAsync(sb, s);
+        release_stage();
         free_ctx(c, s);
         return st;
     }
-    c->bytes += 0;
-    const double *da = a, *db = b;
     auto fail = [&](int code) {
-        if (sa) cudaFreeAsync(sa, s);
-        if (sb) cudaFreeAsync(sb, s);
+        release_stage();
         free_ctx(c, s);
         return code;
     };
-    if (ha) {
-        if (cudaMemcpyAsync(sa, a, z.grid, cudaMemcpyHostToDevice, s) != cudaSuccess) return fail(LSG_ERR_CUDA);
-        da = sa;
-    }
-    if (hb) {
-        if (cudaMemcpyAsync(sb, b, z.grid, cudaMemcpyHostToDevice, s) != cudaSuccess) return fail(LSG_ERR_CUDA);
-        db = sb;
-    }
+    for (int k = 0; k < 4; ++k)
+        if (stage[k] && cudaMemcpyAsync(stage[k], host_in[k], z.grid, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return fail(LSG_ERR_CUDA);
+    const double *da[3] = {dev_in[0], dev_in[1], dev_in[2]}, *db = dev_in[3];
     if (cudaMemsetAsync(c->err, 0, sizeof(int) * 4, s) != cudaSuccess) return fail(LSG_ERR_CUDA);
     st = build_tables(c, da, db, s);
     if (st != LSG_OK) return fail(st);
@@ -408,14 +466,38 @@ int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, con
     if (derr != LSG_OK) return fail(derr);
     st = build_preconditioner(c, s);
     if (st != LSG_OK) return fail(st);
-    if (sa) cudaFreeAsync(sa, s);
-    if (sb) cudaFreeAsync(sb, s);
-    sa = sb = nullptr;
+    release_stage();
     derr = read_dev_error(c, s);
     if (derr == LSG_ERR_TIMEOUT || derr == LSG_ERR_CUDA) return fail(derr);
     c->setup_status = derr;
     *out = c;
     return derr;  // LSG_OK or LSG_ERR_ILU_BREAKDOWN (context kept for inspection)
+}
+
+int lsg_setup_ex(lsg_ctx **out, int d, int N, int T, int Q, const double *a, const double *b, int precision,
+                 unsigned flags, lsg_stream_t stream)
+{
+    if (!a || T < 0 || T > 64) return LSG_ERR_ARG;
+    int ta[3][3], tb[3];
+    for (int j = 0; j < 3; ++j) {
+        tb[j] = T;
+        for (int i = 0; i < 3; ++i) ta[j][i] = T;
+    }
+    const double *ad[3] = {a, a, a};
+    return setup_impl(out, d, N, ta, tb, Q, ad, b, precision, flags, (cudaStream_t)stream);
+}
+
+int lsg_setup_problem(lsg_ctx **out, const lsg_problem *p, lsg_stream_t stream)
+{
+    if (!p || p->d < 1 || p->d > 3) return LSG_ERR_ARG;
+    int ta[3][3], tb[3];
+    const double *ad[3];
+    for (int j = 0; j < 3; ++j) {
+        tb[j] = p->tb[j];
+        ad[j] = (j < p->d && p->a[j]) ? p->a[j] : p->a[0];
+        for (int i = 0; i < 3; ++i) ta[j][i] = p->ta[j][i];
+    }
+    return setup_impl(out, p->d, p->N, ta, tb, p->Q, ad, p->b, p->precision, p->flags, (cudaStream_t)stream);
 }
 
 int lsg_setup(lsg_ctx **out, int d, int N, int T, int Q, const double *a, const double *b, int precision,
@@ -553,6 +635,8 @@ long long lsg_export_count(lsg_ctx *c, int item)
     case LSG_EXPORT_GAUSS_X:
     case LSG_EXPORT_GAUSS_W: return g.Q;
     case LSG_EXPORT_AHAT:
+    case LSG_EXPORT_AHAT_Y:
+    case LSG_EXPORT_AHAT_Z:
     case LSG_EXPORT_BHAT: return ns;
     case LSG_EXPORT_BAND_S:
     case LSG_EXPORT_BAND_M: return (long long)(g.T + 1) * g.n1 * g.W1;
@@ -572,6 +656,8 @@ int lsg_export(lsg_ctx *c, int item, double *out)
     case LSG_EXPORT_GAUSS_X: src = c->gx; break;
     case LSG_EXPORT_GAUSS_W: src = c->gw; break;
     case LSG_EXPORT_AHAT: src = c->ahat; break;
+    case LSG_EXPORT_AHAT_Y: src = c->ahaty; break;
+    case LSG_EXPORT_AHAT_Z: src = c->ahatz; break;
     case LSG_EXPORT_BHAT: src = c->bhat; break;
     case LSG_EXPORT_BAND_S: src = c->bandS; break;
     case LSG_EXPORT_BAND_M: src = c->bandM; break;

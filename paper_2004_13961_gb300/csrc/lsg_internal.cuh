@@ -49,9 +49,14 @@ struct Geom {
     long long nlines;     // n1^(d-1)
     int levels;           // wavefront levels (n1-1) * sum_{a<d} (w+1)^a + 1
     int has_b;            // reaction term present (pattern includes the mass term)
+    // truncation degrees: ta[j][i] of the series of a_j (the coefficient of the j-th
+    // gradient term) in direction i, tb[i] of b's; T is the largest, w the half-width
+    // of the offset box that holds every band of the pattern
+    int ta[3][3], tb[3];
 };
 
 Geom make_geom(int d, int N, int T, int Q);
+Geom make_geom_dir(int d, int N, const int ta[3][3], const int tb[3], int Q);
 
 // pinned + device scalars of one PCG run (device-resident Algorithm 1 state)
 struct PcgState {
@@ -97,10 +102,14 @@ struct lsg_ctx {
     double *gx, *gw;           // Q nodes / weights
     double *tab;               // 4 blocks of QhP*KP: phiE, phiO, dphiE, dphiO
     double *Wa, *Wb, *Wg;      // w(x)w(y)w(z) * a, * b, and the weights alone (Q^d)
+    double *Way, *Waz;         // W * a_y, W * a_z (aliases of Wa for one diffusion coefficient)
     float *Wa32, *Wb32;        // FP32 copies (mixed)
+    float *Wa32y, *Wa32z;
+    int own_ay, own_az;        // Way / Waz (and their FP32 copies, series) are separate arrays
     void *tct;                 // mixed: unfolded TF32/BF16 tables for the tensor-core contractions
     int tcMpF, tcKpF, tcMpB, tcKpB;  // their padded shapes (forward [MpF][KpF], backward [MpB][KpB])
-    double *ahat, *bhat;       // (T+1)^d
+    double *ahat, *bhat;       // (T+1)^d, zero beyond each direction's degree
+    double *ahaty, *ahatz;     // series of a_y, a_z (aliases of ahat for one coefficient and degree)
     double *bandS, *bandM;     // (T+1) x n1 x W1
 
     // ILU(0) factors in split stencil storage: Lv [n][SL] strictly lower slots,
@@ -147,7 +156,7 @@ int dalloc(lsg_ctx *c, void **p, size_t bytes, cudaStream_t s);
 bool is_device_ptr(const void *p);
 
 // kernels / drivers implemented in the .cu files
-int build_tables(lsg_ctx *c, const double *a_dev, const double *b_dev, cudaStream_t s);
+int build_tables(lsg_ctx *c, const double *const *a_dev, const double *b_dev, cudaStream_t s);
 int build_preconditioner(lsg_ctx *c, cudaStream_t s);
 int apply_K(lsg_ctx *c, const double *x, double *y, const int *done, cudaStream_t s);
 int apply_K_tc(lsg_ctx *c, const float *x, float *y, const int *done, cudaStream_t s);

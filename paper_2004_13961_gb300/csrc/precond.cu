@@ -21,13 +21,17 @@ namespace lsg {
 
 // ---------------------------------------------------------------------------
 // M assembly.  With band matrices S^(t)[i][o], M^(t)[i][o] (o = column - row),
-// `2DM` in Kronecker form (Sec. 4.2) gives for row (i,j), offset (ox,oy):
+// `2DM` in Kronecker form (Sec. 4.2), with the series a_x, a_y of the two gradient
+// terms (the same one for a scalar coefficient) and b, gives for row (i,j),
+// offset (ox,oy):
 //   M = sum_k [ M^(k)[j][oy] X1[k][i][ox] + S^(k)[j][oy] X2[k][i][ox] ],
-//   X1[k][i][ox] = sum_t (a_tk S^(t)[i][ox] + b_tk M^(t)[i][ox]),
-//   X2[k][i][ox] = sum_t a_tk M^(t)[i][ox]          (t: x degree, k: y degree)
-// and `3DM` similarly with a second contraction over the z degree.
-__global__ void k_precontract(int d, int T, int n1, int W1, const double *ahat, const double *bhat,
-                              int has_b, const double *bS, const double *bM, double *X1, double *X2)
+//   X1[k][i][ox] = sum_t (ax_tk S^(t)[i][ox] + b_tk M^(t)[i][ox]),
+//   X2[k][i][ox] = sum_t ay_tk M^(t)[i][ox]          (t: x degree, k: y degree)
+// and `3DM` similarly with a second contraction over the z degree and a third
+// array X3 (the series of a_z).  Series are zero beyond their degrees.
+__global__ void k_precontract(int d, int T, int n1, int W1, const double *ahx, const double *ahy,
+                              const double *ahz, const double *bhat, int has_b, const double *bS,
+                              const double *bM, double *X1, double *X2, double *X3)
 {
     // X[K][i][o] with K = (k) in 2D or (k,l) in 3D, (T+1)^(d-1) values of K
     int T1 = T + 1;
@@ -38,21 +42,23 @@ __global__ void k_precontract(int d, int T, int n1, int W1, const double *ahat, 
     int o = (int)(idx % W1);
     int i = (int)((idx / W1) % n1);
     long long K = idx / ((long long)W1 * n1);
-    double x1 = 0.0, x2 = 0.0;
+    double x1 = 0.0, x2 = 0.0, x3 = 0.0;
     for (int t = 0; t < T1; ++t) {
-        double at = ahat[K * T1 + t], bt = bhat[K * T1 + t];
+        double bt = bhat[K * T1 + t];
         double s = bS[((size_t)t * n1 + i) * W1 + o], m = bM[((size_t)t * n1 + i) * W1 + o];
-        x1 += at * s + (has_b ? bt * m : 0.0);
-        x2 += at * m;
+        x1 += ahx[K * T1 + t] * s + (has_b ? bt * m : 0.0);
+        x2 += ahy[K * T1 + t] * m;
+        if (X3) x3 += ahz[K * T1 + t] * m;
     }
     X1[idx] = x1;
     X2[idx] = x2;
+    if (X3) X3[idx] = x3;
 }
 
 template <typename V>
 __global__ void k_assemble(StencilGeo G, const double *ahat, const double *bhat, const double *bS,
-                           const double *bM, const double *X1, const double *X2, V *Lv, V *Uv,
-                           double *Mkeep)
+                           const double *bM, const double *X1, const double *X2, const double *X3, V *Lv,
+                           V *Uv, double *Mkeep)
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= G.n * G.S) return;
@@ -87,7 +93,7 @@ __global__ void k_assemble(StencilGeo G, const double *ahat, const double *bhat,
                     size_t by = ((size_t)kk * n1 + j) * W1 + dy + w;
                     size_t bx = (((size_t)l * T1 + kk) * n1 + i) * W1 + dx + w;
                     double my = bM[by], sy = bS[by];
-                    v += my * mz * X1[bx] + (sy * mz + my * sz) * X2[bx];
+                    v += my * mz * X1[bx] + sy * mz * X2[bx] + my * sz * X3[bx];
                 }
             }
         }
@@ -471,7 +477,7 @@ static int assemble_and_factor(lsg_ctx *c, cudaStream_t s)
     StencilGeo G = sgeo(g);
     int T1 = g.T + 1;
     long long nK = (g.d == 3) ? (long long)T1 * T1 : T1;
-    double *X1 = nullptr, *X2 = nullptr;
+    double *X1 = nullptr, *X2 = nullptr, *X3 = nullptr;
     cudaEvent_t e0, e1, e2;
     LSG_CK(cudaEventCreate(&e0));
     LSG_CK(cudaEventCreate(&e1));
@@ -481,9 +487,11 @@ static int assemble_and_factor(lsg_ctx *c, cudaStream_t s)
         size_t nx = (size_t)nK * g.n1 * g.W1;
         LSG_CK(cudaMallocAsync((void **)&X1, sizeof(double) * nx, s));
         LSG_CK(cudaMallocAsync((void **)&X2, sizeof(double) * nx, s));
+        if (g.d == 3) LSG_CK(cudaMallocAsync((void **)&X3, sizeof(double) * nx, s));
         ::lsg::count_launch();
-        k_precontract<<<(unsigned)((nx + 255) / 256), 256, 0, s>>>(g.d, g.T, g.n1, g.W1, c->ahat, c->bhat,
-                                                                   g.has_b, c->bandS, c->bandM, X1, X2);
+        k_precontract<<<(unsigned)((nx + 255) / 256), 256, 0, s>>>(g.d, g.T, g.n1, g.W1, c->ahat, c->ahaty,
+                                                                   c->ahatz, c->bhat, g.has_b, c->bandS,
+                                                                   c->bandM, X1, X2, X3);
         LSG_CK(cudaGetLastError());
     }
     LSG_CK(cudaMemsetAsync(c->Lv, 0, sizeof(V) * (size_t)g.n * g.SL, s));
@@ -491,10 +499,11 @@ static int assemble_and_factor(lsg_ctx *c, cudaStream_t s)
     long long tot = g.n * g.S;
     ::lsg::count_launch();
     k_assemble<V><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(G, c->ahat, c->bhat, c->bandS, c->bandM, X1, X2,
-                                                               (V *)c->Lv, (V *)c->Uv, c->Mkeep);
+                                                               X3, (V *)c->Lv, (V *)c->Uv, c->Mkeep);
     LSG_CK(cudaGetLastError());
     if (X1) LSG_CK(cudaFreeAsync(X1, s));
     if (X2) LSG_CK(cudaFreeAsync(X2, s));
+    if (X3) LSG_CK(cudaFreeAsync(X3, s));
 
     // wavefront order
     int *cnt = nullptr;

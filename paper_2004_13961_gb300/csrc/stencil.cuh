@@ -12,11 +12,17 @@ namespace lsg {
 struct StencilGeo {
     int d, n1, w, W1, S, Sc, SL, SU, T, has_b;
     long long n, nlines;
+    signed char ta[9], tb[3];  // truncation degrees: ta[3 j + i] of a_j in direction i, tb[i] of b
 };
 
 static inline StencilGeo sgeo(const Geom &g)
 {
-    return StencilGeo{g.d, g.n1, g.w, g.W1, g.S, g.Sc, g.SL, g.SU, g.T, g.has_b, g.n, g.nlines};
+    StencilGeo G{g.d, g.n1, g.w, g.W1, g.S, g.Sc, g.SL, g.SU, g.T, g.has_b, g.n, g.nlines, {}, {}};
+    for (int j = 0; j < 3; ++j) {
+        G.tb[j] = (signed char)g.tb[j];
+        for (int i = 0; i < 3; ++i) G.ta[3 * j + i] = (signed char)g.ta[j][i];
+    }
+    return G;
 }
 
 __device__ __forceinline__ void slot_offsets(const StencilGeo &G, int s, int &dx, int &dy, int &dz)
@@ -31,9 +37,11 @@ __device__ __forceinline__ int slot_index(const StencilGeo &G, int dx, int dy, i
 }
 
 // Structural pattern of M (reading of NZ(M) in Sec. 4.2): union over the
-// Kronecker terms of their band supports.  One direction carries a stiffness
-// band (|o| <= T), the others mass bands (|o| <= T+2; only even offsets when
-// T = 0); the reaction term, when present, has mass bands in every direction.
+// Kronecker terms of their band supports.  Term j (stiffness in direction j, the
+// series of a_j) has a stiffness band (|o| <= degree) in direction j and mass
+// bands (|o| <= degree + 2; only even offsets for degree 0) in the others, each
+// with a_j's degree in that direction; the reaction term, when present, has mass
+// bands of b's degrees in every direction.
 __device__ __forceinline__ bool stiff_band(int o, int T) { return o <= T && o >= -T; }
 __device__ __forceinline__ bool mass_band(int o, int T)
 {
@@ -43,15 +51,16 @@ __device__ __forceinline__ bool mass_band(int o, int T)
 __device__ inline bool structural(const StencilGeo &G, int dx, int dy, int dz)
 {
     int o[3] = {dx, dy, dz};
-    bool mm = true;
-    for (int a = 0; a < G.d; ++a) mm = mm && mass_band(o[a], G.T);
-    if (G.has_b && mm) return true;
-    for (int a = 0; a < G.d; ++a) {
-        if (!stiff_band(o[a], G.T)) continue;
-        bool ok = true;
-        for (int b = 0; b < G.d; ++b)
-            if (b != a && !mass_band(o[b], G.T)) ok = false;
+    for (int j = 0; j < G.d; ++j) {
+        bool ok = stiff_band(o[j], G.ta[3 * j + j]);
+        for (int i = 0; i < G.d && ok; ++i)
+            if (i != j) ok = mass_band(o[i], G.ta[3 * j + i]);
         if (ok) return true;
+    }
+    if (G.has_b) {
+        bool mm = true;
+        for (int i = 0; i < G.d; ++i) mm = mm && mass_band(o[i], G.tb[i]);
+        if (mm) return true;
     }
     return false;
 }

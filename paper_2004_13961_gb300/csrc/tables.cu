@@ -13,14 +13,40 @@ namespace lsg {
 
 Geom make_geom(int d, int N, int T, int Q)
 {
+    int ta[3][3], tb[3];
+    for (int j = 0; j < 3; ++j) {
+        tb[j] = T;
+        for (int i = 0; i < 3; ++i) ta[j][i] = T;
+    }
+    return make_geom_dir(d, N, ta, tb, Q);
+}
+
+// Degrees per coefficient and direction (Sec. 4.1's t_1 for a and t_2 for b; Sec. 5
+// Example 4's t_1j for a_j): T is the largest degree (the size of the series and
+// band tables), w the half-width of the offset box that holds every band of the
+// pattern: a stiffness band reaches its degree, a mass band its degree + 2.
+Geom make_geom_dir(int d, int N, const int ta[3][3], const int tb[3], int Q)
+{
     Geom g{};
     g.d = d;
     g.N = N;
     g.n1 = N - 1;
     g.Q = Q;
     g.Qh = (Q + 1) / 2;
-    g.T = T;
-    g.w = T + 2;
+    g.T = 0;
+    g.w = 0;
+    for (int j = 0; j < 3; ++j) {
+        g.tb[j] = j < d ? tb[j] : 0;
+        for (int i = 0; i < 3; ++i) g.ta[j][i] = (i < d && j < d) ? ta[j][i] : 0;
+    }
+    for (int i = 0; i < d; ++i) {
+        g.T = std::max(g.T, g.tb[i]);
+        g.w = std::max(g.w, g.tb[i] + 2);
+        for (int j = 0; j < d; ++j) {
+            g.T = std::max(g.T, g.ta[j][i]);
+            g.w = std::max(g.w, i == j ? g.ta[j][i] : g.ta[j][i] + 2);
+        }
+    }
     g.W1 = 2 * g.w + 1;
     g.S = 1;
     for (int i = 0; i < d; ++i) g.S *= g.W1;
@@ -171,6 +197,22 @@ __global__ void k_weighted(int d, int Q, long long nq, const double *w, const do
     Wg[g] = W;
 }
 
+// Wd = W c for a further diffusion coefficient (one per direction).
+__global__ void k_weighted_dir(int d, int Q, long long nq, const double *w, const double *c, double *Wd, int *err)
+{
+    long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (g >= nq) return;
+    long long rem = g;
+    double W = 1.0;
+    for (int ax = 0; ax < d; ++ax) {
+        W *= w[rem % Q];
+        rem /= Q;
+    }
+    const double v = c[g];
+    if (!isfinite(v)) set_err(err, DERR_NONFINITE);
+    Wd[g] = W * v;
+}
+
 __global__ void k_to_float(long long n, const double *a, float *b)
 {
     long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -215,18 +257,22 @@ __global__ void k_contract_lw(long long R, int Q, int T1, const double *in, cons
     out[(size_t)t * R + r] = s;
 }
 
-__global__ void k_scale_series(int d, int T1, double *chat)
+// The (2t+1)/2 factors of the discrete Legendre transform; terms of degree above
+// the series' degree in some direction are dropped (the truncation, per direction).
+__global__ void k_scale_series(int d, int T1, int deg0, int deg1, int deg2, double *chat)
 {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     int tot = 1;
     for (int i = 0; i < d; ++i) tot *= T1;
     if (idx >= tot) return;
+    const int deg[3] = {deg0, deg1, deg2};
     int rem = idx;
     double f = 1.0;
     for (int ax = 0; ax < d; ++ax) {
         int t = rem % T1;
         rem /= T1;
         f *= (2.0 * t + 1.0) * 0.5;
+        if (t > deg[ax]) f = 0.0;
     }
     chat[idx] *= f;
 }
@@ -295,8 +341,9 @@ int gauss_rule(int Q, double *x, double *w, cudaStream_t s)
 
 // Build every table a context needs before the preconditioner: Gauss rule,
 // folded basis tables, weighted samples, a_hat, b_hat and the band matrices.
-int build_tables(lsg_ctx *c, const double *a_dev, const double *b_dev, cudaStream_t s)
+int build_tables(lsg_ctx *c, const double *const *a_dir, const double *b_dev, cudaStream_t s)
 {
+    const double *a_dev = a_dir[0];
     const Geom &g = c->g;
     ::lsg::count_launch();
     k_gauss<<<blocks_for(g.Qh, 128), 128, 0, s>>>(g.Q, c->gx, c->gw);
@@ -309,11 +356,29 @@ int build_tables(lsg_ctx *c, const double *a_dev, const double *b_dev, cudaStrea
                                                       c->Wg, c->err);
     LSG_CK(cudaGetLastError());
 
+    // one diffusion coefficient per direction: the others' weighted samples
+    if (c->own_ay) {
+        ::lsg::count_launch();
+        k_weighted_dir<<<blocks_for(g.nq, 256), 256, 0, s>>>(g.d, g.Q, g.nq, c->gw, a_dir[1], c->Way, c->err);
+    }
+    if (c->own_az) {
+        ::lsg::count_launch();
+        k_weighted_dir<<<blocks_for(g.nq, 256), 256, 0, s>>>(g.d, g.Q, g.nq, c->gw, a_dir[2], c->Waz, c->err);
+    }
+    LSG_CK(cudaGetLastError());
     if (c->Wa32) {
         ::lsg::count_launch();
         k_to_float<<<blocks_for(g.nq, 256), 256, 0, s>>>(g.nq, c->Wa, c->Wa32);
         ::lsg::count_launch();
         k_to_float<<<blocks_for(g.nq, 256), 256, 0, s>>>(g.nq, c->Wb, c->Wb32);
+        if (c->own_ay) {
+            ::lsg::count_launch();
+            k_to_float<<<blocks_for(g.nq, 256), 256, 0, s>>>(g.nq, c->Way, c->Wa32y);
+        }
+        if (c->own_az) {
+            ::lsg::count_launch();
+            k_to_float<<<blocks_for(g.nq, 256), 256, 0, s>>>(g.nq, c->Waz, c->Wa32z);
+        }
         LSG_CK(cudaGetLastError());
     }
     // has_b: any nonzero b sample
@@ -335,9 +400,14 @@ int build_tables(lsg_ctx *c, const double *a_dev, const double *b_dev, cudaStrea
     LSG_CK(cudaMallocAsync((void **)&t1, sizeof(double) * big, s));
     ::lsg::count_launch();
     k_lw<<<blocks_for(g.Q, 128), 128, 0, s>>>(g.Q, g.T, c->gx, c->gw, Lw);
-    for (int which = 0; which < 2; ++which) {
-        const double *src = which ? b_dev : a_dev;
-        double *dst = which ? c->bhat : c->ahat;
+    // series of b, a_x, and (when they are separate) a_y, a_z, each with its degrees
+    for (int which = 0; which < 4; ++which) {
+        const double *src = which == 0 ? b_dev : a_dir[which - 1];
+        double *dst = which == 0 ? c->bhat : which == 1 ? c->ahat : which == 2 ? c->ahaty : c->ahatz;
+        const int *deg = which == 0 ? g.tb : g.ta[which - 1];
+        if (which >= 1 && which - 1 >= g.d) break;
+        if (which == 2 && dst == c->ahat) continue;  // the same series as a_x
+        if (which == 3 && (dst == c->ahat || dst == c->ahaty)) continue;
         long long R = g.nq / g.Q;  // rows of the current [R][Q] view
         const double *in = src;
         double *bufs[2] = {t0, t1};
@@ -354,7 +424,7 @@ int build_tables(lsg_ctx *c, const double *a_dev, const double *b_dev, cudaStrea
         }
         ::lsg::count_launch();
         k_scale_series<<<blocks_for(g.d == 1 ? T1 : g.d == 2 ? T1 * T1 : T1 * T1 * T1, 128), 128, 0, s>>>(
-            g.d, T1, dst);
+            g.d, T1, deg[0], deg[1], deg[2], dst);
         LSG_CK(cudaGetLastError());
     }
     LSG_CK(cudaFreeAsync(Lw, s));

@@ -430,7 +430,7 @@ static int apply_K_tc_t(lsg_ctx *c, const float *x, float *y, const int *done, c
     const Geom &g = c->g;
     const long long Q = g.Q, n1 = g.n1;
     float *ws = c->ws32;
-    const float *Wa = c->Wa32, *Wb = c->Wb32;
+    const float *Wa = c->Wa32, *Way = c->Wa32y, *Waz = c->Wa32z, *Wb = c->Wb32;  // W a_j per gradient term
     TcBuilder<OP> T{c, {}, true};
     if (g.d == 1) {
         float *H = ws, *Gx = ws + Q;
@@ -452,7 +452,7 @@ static int apply_K_tc_t(lsg_ctx *c, const float *x, float *y, const int *done, c
         LSG_TRY(T.launch(s));
         T.fwd(Q, done);  // contract y, pointwise W a / W b
         T.out(H, Wb, AP, 0);
-        T.out(Gy, Wa, AP, 1);
+        T.out(Gy, Way, AP, 1);
         T.out(Gx, Wa, AD, 0);
         LSG_TRY(T.launch(s));
         T.bwd(Q, done);  // back over x nodes
@@ -478,8 +478,8 @@ static int apply_K_tc_t(lsg_ctx *c, const float *x, float *y, const int *done, c
     LSG_TRY(T.launch(s));
     T.fwd(Q * Q, done);
     T.out(H, Wb, B0, 0);
-    T.out(Gz, Wa, B0, 1);
-    T.out(Gy, Wa, B1, 0);
+    T.out(Gz, Waz, B0, 1);
+    T.out(Gy, Way, B1, 0);
     T.out(Gx, Wa, B2, 0);
     LSG_TRY(T.launch(s));
     float *Pa = B0, *Pb = B1, *Pc = B2;

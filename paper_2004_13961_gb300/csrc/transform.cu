@@ -318,7 +318,7 @@ size_t workspace_elems(const Geom &g)
 // y = K x (Sec. 4.3), every stage on the device.  `done` (optional) makes every
 // kernel a no-op once a device-side PCG has converged.
 template <typename T>
-static int apply_K_t(lsg_ctx *c, const T *x, T *y, const int *done, T *ws, const T *Wa, const T *Wb,
+static int apply_K_t(lsg_ctx *c, const T *x, T *y, const int *done, T *ws, const T *const *Wd, const T *Wb,
                      cudaStream_t s)
 {
     const Geom &g = c->g;
@@ -329,7 +329,7 @@ static int apply_K_t(lsg_ctx *c, const T *x, T *y, const int *done, T *ws, const
         T *H = ws, *Gx = ws + Q;
         job_init(j, c, 1, done);
         add_out(j, H, Wb, x, 0);
-        add_out(j, Gx, Wa, x, 1);
+        add_out(j, Gx, Wd[0], x, 1);
         LSG_TRY(launch_fwd(j, s, vf[0]));
         job_init(j, c, 1, done);
         add_out(j, y, nullptr, H, 0, Gx, 1);
@@ -345,8 +345,8 @@ static int apply_K_t(lsg_ctx *c, const T *x, T *y, const int *done, T *ws, const
         LSG_TRY(launch_fwd(j, s, vf[0]));
         job_init(j, c, Q, done);                      // contract y: A[q][j]
         add_out(j, H, Wb, AP, 0);
-        add_out(j, Gy, Wa, AP, 1);
-        add_out(j, Gx, Wa, AD, 0);
+        add_out(j, Gy, Wd[1], AP, 1);
+        add_out(j, Gx, Wd[0], AD, 0);
         LSG_TRY(launch_fwd(j, s, vf[1]));
         job_init(j, c, Q, done);                      // contract x-nodes: [r][q]
         add_out(j, P1, nullptr, H, 0, Gx, 1);
@@ -372,9 +372,9 @@ static int apply_K_t(lsg_ctx *c, const T *x, T *y, const int *done, T *ws, const
     LSG_TRY(launch_fwd(j, s, vf[1]));
     job_init(j, c, Q * Q, done);                   // z: [r][q][l] -> [s][r][q]
     add_out(j, H, Wb, B0, 0);
-    add_out(j, Gz, Wa, B0, 1);
-    add_out(j, Gy, Wa, B1, 0);
-    add_out(j, Gx, Wa, B2, 0);
+    add_out(j, Gz, Wd[2], B0, 1);
+    add_out(j, Gy, Wd[1], B1, 0);
+    add_out(j, Gx, Wd[0], B2, 0);
     LSG_TRY(launch_fwd(j, s, vf[2]));
     T *Pa = B0, *Pb = B1, *Pc = B2;           // [n1][Q][Q] = [m][s][r]
     job_init(j, c, Q * Q, done);
@@ -394,7 +394,8 @@ static int apply_K_t(lsg_ctx *c, const T *x, T *y, const int *done, T *ws, const
 
 int apply_K(lsg_ctx *c, const double *x, double *y, const int *done, cudaStream_t s)
 {
-    return apply_K_t<double>(c, x, y, done, c->ws, c->Wa, c->Wb, s);
+    const double *Wd[3] = {c->Wa, c->Way, c->Waz};  // W a_j of the j-th gradient term
+    return apply_K_t<double>(c, x, y, done, c->ws, Wd, c->Wb, s);
 }
 
 

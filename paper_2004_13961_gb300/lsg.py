@@ -26,6 +26,7 @@ SETUP_AUTOTUNE = 4
 
 EXPORT_GAUSS_X, EXPORT_GAUSS_W, EXPORT_AHAT, EXPORT_BHAT = 0, 1, 2, 3
 EXPORT_BAND_S, EXPORT_BAND_M, EXPORT_M, EXPORT_LU = 4, 5, 6, 7
+EXPORT_AHAT_Y, EXPORT_AHAT_Z = 8, 9
 
 Q_UNKNOWNS, Q_GRID, Q_HALF_WIDTH, Q_SLOTS, Q_LEVELS, Q_DEVICE_BYTES, Q_NNZ, Q_PRECISION, Q_ASSEMBLE_US, Q_ILU_US = \
     range(10)
@@ -38,7 +39,7 @@ OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_ILU_BREAKDOWN, ERR_NOT_CONVERGED, ERR_TIME
 # every symbol the header declares (checked by the ABI test)
 SYMBOLS = [
     "lsg_version", "lsg_status_string", "lsg_last_error", "lsg_kernel_launches", "lsg_gauss", "lsg_gauss_noalloc", "lsg_footprint_bytes",
-    "lsg_setup", "lsg_setup_ex", "lsg_load_vector", "lsg_apply_A", "lsg_apply_A_lowp", "lsg_apply_Minv",
+    "lsg_setup", "lsg_setup_ex", "lsg_setup_problem", "lsg_load_vector", "lsg_apply_A", "lsg_apply_A_lowp", "lsg_apply_Minv",
     "lsg_pcg_solve",
     "lsg_eval", "lsg_export_count", "lsg_export", "lsg_query", "lsg_destroy", "lsg_set_wait_budget",
     "lsg_autotune_transforms", "lsg_transform_tiles", "lsg_set_transform_tiles",
@@ -55,6 +56,12 @@ class LsgInfo(ctypes.Structure):
     def as_dict(self):
         return dict(iters=self.iters, outer_iters=self.outer_iters, relres=self.relres,
                     relres_true=self.relres_true, status=self.status)
+
+
+class LsgProblem(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("N", ctypes.c_int), ("Q", ctypes.c_int),
+                ("a", ctypes.c_void_p * 3), ("b", ctypes.c_void_p), ("ta", (ctypes.c_int * 3) * 3),
+                ("tb", ctypes.c_int * 3), ("precision", ctypes.c_int), ("flags", ctypes.c_uint)]
 
 
 class LsgRequest(ctypes.Structure):
@@ -98,6 +105,7 @@ def load(build_if_needed: bool = True):
     L.lsg_footprint_bytes.restype = ctypes.c_size_t
     L.lsg_setup.argtypes = [ctypes.POINTER(vp), ci, ci, ci, ci, vp, vp, ci, vp]
     L.lsg_setup_ex.argtypes = [ctypes.POINTER(vp), ci, ci, ci, ci, vp, vp, ci, cu, vp]
+    L.lsg_setup_problem.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(LsgProblem), vp]
     for name in ("lsg_load_vector", "lsg_apply_A", "lsg_apply_A_lowp", "lsg_apply_Minv", "lsg_eval"):
         getattr(L, name).argtypes = [vp, vp, vp, vp]
     L.lsg_pcg_solve.argtypes = [vp, vp, vp, cd, ci, ctypes.POINTER(LsgInfo), vp]
@@ -199,17 +207,33 @@ class Context:
     """An lsg_ctx: tables, coefficient samples, M's ILU(0) factors and workspaces."""
 
     def __init__(self, d, N, T, a, b, Q=None, precision=FP64, keep_M=False, stream=None, allow_breakdown=False,
-                 profile=False, autotune=False):
+                 profile=False, autotune=False, ta=None, tb=None):
+        """A context for lsg_setup_ex (one coefficient a, one degree T), or -- when `a` is a list
+        of d per-direction coefficients or the degrees ta (d x d: ta[j][i] of a_j in direction
+        i) and tb (d) are given -- for lsg_setup_problem (T unused then)."""
         L = load()
         self._L = L
         self.d, self.N, self.T = d, N, T
         self.Q = N + 2 if Q is None else Q
         self.precision = precision
         h = ctypes.c_void_p(0)
-        st = L.lsg_setup_ex(ctypes.byref(h), d, N, T, self.Q, _ptr(a), _ptr(b), precision,
-                            (SETUP_KEEP_M if keep_M else 0) | (SETUP_PROFILE if profile else 0)
-                            | (SETUP_AUTOTUNE if autotune else 0),
-                            _stream(stream))
+        flags = (SETUP_KEEP_M if keep_M else 0) | (SETUP_PROFILE if profile else 0) | (SETUP_AUTOTUNE if autotune else 0)
+        if isinstance(a, (list, tuple)) or ta is not None or tb is not None:
+            alist = list(a) if isinstance(a, (list, tuple)) else [a] * d
+            ta = [[T] * d for _ in range(d)] if ta is None else ta
+            tb = [T] * d if tb is None else tb
+            pr = LsgProblem()
+            pr.d, pr.N, pr.Q, pr.precision, pr.flags = d, N, self.Q, precision, flags
+            for j in range(3):
+                pr.a[j] = _ptr(alist[j]).value if j < len(alist) else None
+                pr.tb[j] = int(tb[j]) if j < d else 0
+                for i in range(3):
+                    pr.ta[j][i] = int(ta[j][i]) if (j < d and i < d) else 0
+            pr.b = _ptr(b).value
+            self._keep = (alist, b)
+            st = L.lsg_setup_problem(ctypes.byref(h), ctypes.byref(pr), _stream(stream))
+        else:
+            st = L.lsg_setup_ex(ctypes.byref(h), d, N, T, self.Q, _ptr(a), _ptr(b), precision, flags, _stream(stream))
         self.status = st
         self._h = h
         if st != OK and not (allow_breakdown and st == ERR_ILU_BREAKDOWN and h.value):

@@ -224,3 +224,35 @@ def polynomial_coefficient_problem(d: int, N: int, T: int, deg_a: int, deg_b: in
     f = rhs_samples_from_coeffs(d, Q, fc)
     return dict(name=f"poly-{d}d-N{N}", d=d, N=N, Q=Q, T=T, a=a, b=b, f=f,
                 fcoef=coeffs_fastest_first(fc), f_deg=min(N, 12))
+
+
+def grid_coords(d: int, Q: int) -> list:
+    """Coordinates of the Q^d tensor Gauss grid (x fastest): [x, y, z][:d], each Q^d long."""
+    x = nodes(Q)
+    mesh = np.meshgrid(*([x] * d), indexing="ij")  # mesh[k] varies along array axis k (axis 0 slowest)
+    return [mesh[d - 1 - i].ravel() for i in range(d)]
+
+
+def paper_example(example: str, d: int, N: int) -> dict:
+    """The coefficients of the paper's iteration experiments (Sec. 5, Examples 1-4) on the
+    N+1-point Gauss grid the paper uses.  Example "a": beta = (2|x|^2 + 1)^4, alpha =
+    cos(x + y + z) (d = 1, 2, 3 as Examples 1-3); "b": beta = exp(2(x + y + z)), alpha = 0;
+    "4": Example 4, one coefficient per direction, beta_1 = exp(2x), beta_2 = cos(y),
+    beta_3 = cos(z), alpha = 0.  The paper states neither f nor x0: f = 1, x0 = 0 here.
+    Returns a (list of d per-direction samples), b, f and Q."""
+    Q = N + 1
+    g = grid_coords(d, Q)
+    s = sum(g)
+    if example == "a":
+        beta = (2.0 * sum(v * v for v in g) + 1.0) ** 4
+        a = [beta] * d
+        b = np.cos(s)
+    elif example == "b":
+        a = [np.exp(2.0 * s)] * d
+        b = np.zeros(Q ** d)
+    elif example == "4":
+        a = [np.exp(2.0 * g[0])] + [np.cos(g[i]) for i in range(1, d)]
+        b = np.zeros(Q ** d)
+    else:
+        raise ValueError(example)
+    return dict(name=f"example-{example}-{d}d-N{N}", d=d, N=N, Q=Q, a=a, b=b, f=np.ones(Q ** d))
