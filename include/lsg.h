@@ -72,6 +72,12 @@ enum lsg_precision {
                                 lsg_pcg_solve launches, with CUDA events recorded on the solve's
                                 stream (no extra synchronisation); read with the LSG_Q_SWEEP_* and
                                 LSG_Q_KX_* queries after the solve returns */
+#define LSG_SETUP_CONST_PRECOND 8u /* PCG-I, the paper's comparison method (Sec. 5): precondition with
+                                      M_0, the operator with every coefficient replaced by the constant
+                                      term of its Legendre series (all truncation degrees 0), solved
+                                      directly in each iteration by fast diagonalisation (generalised
+                                      eigenvectors of the 1D mass and stiffness matrices, computed on the
+                                      device) instead of ILU(0) of M; FP64 contexts only */
 #define LSG_SETUP_AUTOTUNE 4u /* when the committed tile table has no entry for (d, N, Q), time the
                                  tile variants of the FP64 contractions of K x at setup and keep
                                  the fastest (lsg_autotune_transforms) */
@@ -87,7 +93,9 @@ enum lsg_export_item {
     LSG_EXPORT_M = 6,         /* n x S stencil of M (needs LSG_SETUP_KEEP_M) */
     LSG_EXPORT_LU = 7,        /* n x S stencil of the ILU(0) factors (L strictly lower, U upper) */
     LSG_EXPORT_AHAT_Y = 8,    /* truncated series of the y-direction diffusion coefficient (lsg_setup_problem) */
-    LSG_EXPORT_AHAT_Z = 9     /* truncated series of the z-direction diffusion coefficient */
+    LSG_EXPORT_AHAT_Z = 9,    /* truncated series of the z-direction diffusion coefficient */
+    LSG_EXPORT_CONST_EIG = 10 /* LSG_SETUP_CONST_PRECOND: the N-1 generalised eigenvalues of the 1D
+                                 mass and stiffness matrices, index 2k + parity */
 };
 
 /* lsg_query items */
@@ -111,7 +119,10 @@ enum lsg_query_item {
     LSG_Q_KX_US = 14,         /* FP64 matrix-free products inside the PCG loop */
     LSG_Q_KX_CALLS = 15,
     LSG_Q_KX_LO_US = 16,      /* low-precision products of the mixed form's inner PCG */
-    LSG_Q_KX_LO_CALLS = 17
+    LSG_Q_KX_LO_CALLS = 17,
+    LSG_Q_CONST_US = 18,      /* constant-coefficient preconditioner solves (LSG_SETUP_CONST_PRECOND) */
+    LSG_Q_CONST_CALLS = 19,
+    LSG_Q_PRECOND_KIND = 20   /* 0: ILU(0) of M, 1: the constant-coefficient preconditioner */
 };
 
 typedef struct {

@@ -365,3 +365,57 @@ def solve_dir(d, N, Q, a, b, ta, tb, F, eps=1e-12, kmax=10000):
     out.update(st)
     return out
 
+
+
+# --------------------------------------------------------------------------- PCG-I
+# The paper's comparison method (Sec. 5, the PCG-I rows of Tables 5.7-5.11): PCG with a
+# constant-coefficient preconditioner, the system with it as the matrix solved directly in
+# each iteration.  Its matrix is M with every truncation degree 0 (the rows "t_1 = 0,
+# t_2 = 0"): each coefficient replaced by the constant term of its Legendre series.  The
+# oracle solves it with a dense Cholesky factorisation (small sizes only).
+
+
+def setup_const(d, N, Q, a, b):
+    """M_0 (all degrees 0) assembled by Sec. 4.2's Kronecker form, and its Cholesky factor."""
+    a = list(a) if isinstance(a, (list, tuple)) else [a] * d
+    zeros = [[0] * d for _ in range(d)]
+    ahats = [coef_trunc_dir(d, Q, 0, [0] * d, a[j]) for j in range(d)]
+    bhat = coef_trunc_dir(d, Q, 0, [0] * d, b)
+    M0 = assemble_M_dir(d, N, 0, ahats, bhat, zeros, [0] * d, has_b(b))
+    D = M0.to_dense()
+    C = np.linalg.cholesky(D)
+    return dict(M0=M0, dense=D, chol=C, abar=[float(v[0]) for v in ahats], bbar=float(bhat[0]))
+
+
+def pcg_const(d, N, Q, a, b, F, eps=1e-12, kmax=10000, x0=None, setup=None):
+    """Algorithm 1 with z = M_0^{-1} r by the Cholesky factor (the exact direct solve)."""
+    import scipy.linalg as sla
+    a = list(a) if isinstance(a, (list, tuple)) else [a] * d
+    st = setup_const(d, N, Q, a, b) if setup is None else setup
+    C = st["chol"]
+    F = _c64(F)
+    x = np.zeros(_n(d, N)) if x0 is None else _c64(x0).copy()
+    nF = np.linalg.norm(F)
+    r = F - apply_K_dir(d, N, Q, a, b, x)
+    k, rho, p, status = 0, 0.0, None, OR_OK
+    while np.sqrt(r @ r) > eps * nF and k < kmax:
+        z = sla.cho_solve((C, True), r)
+        k += 1
+        if k == 1:
+            p = z.copy()
+            rho = r @ z
+        else:
+            rho_t, rho = rho, r @ z
+            p = z + (rho / rho_t) * p
+        w = apply_K_dir(d, N, Q, a, b, p)
+        pw = p @ w
+        if not pw > 0.0:
+            status = OR_ERR_NOT_CONVERGED
+            break
+        alpha = rho / pw
+        x += alpha * p
+        r -= alpha * w
+    if status == OR_OK and np.sqrt(r @ r) > eps * nF:
+        status = OR_ERR_NOT_CONVERGED
+    rt = np.linalg.norm(F - apply_K_dir(d, N, Q, a, b, x)) / nF
+    return dict(x=x, iters=k, relres=np.sqrt(r @ r) / nF, relres_true=rt, status=status, setup=st)

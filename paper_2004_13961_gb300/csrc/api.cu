@@ -89,8 +89,9 @@ static Sizes sizes_for(const Geom &g, int precision, unsigned flags)
     z.grid = (size_t)g.nq * 8;
     z.series = ns * 8;
     z.band = T1 * g.n1 * g.W1 * 8;
-    z.Lv = (size_t)g.n * g.SL * vsz;
-    z.Uv = (size_t)g.n * g.SU * vsz;
+    const bool cst = (flags & LSG_SETUP_CONST_PRECOND) != 0;  // no factors: M_0 is solved directly
+    z.Lv = cst ? 0 : (size_t)g.n * g.SL * vsz;
+    z.Uv = cst ? 0 : (size_t)g.n * g.SU * vsz;
     z.Mkeep = (flags & LSG_SETUP_KEEP_M) ? (size_t)g.n * g.S * 8 : 0;
     z.ws = workspace_elems(g) * 8;
     z.vec = (size_t)g.n * 8;
@@ -202,7 +203,7 @@ static void free_ctx(lsg_ctx *c, cudaStream_t s)
                     c->Lv, c->Uv, c->Mkeep, c->order, c->rowflag, c->prog, c->counters, c->err, c->ws, c->ws32,
                     c->r, c->z, c->p, c->wv, c->xs, c->fs, c->ys, c->red, c->st, c->r32, c->z32, c->p32, c->w32,
                     c->e32, c->e64, c->u64, c->y32, c->Wa32, c->Wb32, c->tct,
-                    c->Way, c->Waz, c->Wa32y, c->Wa32z, c->ahaty, c->ahatz};
+                    c->Way, c->Waz, c->Wa32y, c->Wa32z, c->ahaty, c->ahatz, c->ctab, c->clam, c->cdinv};
     const int np = (int)(sizeof ptrs / sizeof ptrs[0]);
     for (int i = 0; i < np; ++i) {
         bool dup = false;  // per-direction arrays may alias the first direction's
@@ -318,7 +319,9 @@ static int setup_impl(lsg_ctx **out, int d, int N, const int ta[3][3], const int
     LSG_TRY(check_sizes(d, N, g0.T, Q));
     if (g0.w > 66) return LSG_ERR_ARG;
     if (precision < LSG_FP64 || precision > LSG_MIXED_BF16) return LSG_ERR_ARG;
+    if ((flags & LSG_SETUP_CONST_PRECOND) && precision != LSG_FP64) return LSG_ERR_ARG;
     lsg_ctx *c = new lsg_ctx{};
+    c->precond = (flags & LSG_SETUP_CONST_PRECOND) ? 1 : 0;
     c->stream = s;
     c->g = g0;
     c->precision = precision;
@@ -380,6 +383,11 @@ static int setup_impl(lsg_ctx **out, int d, int N, const int ta[3][3], const int
     ALLOC(c->bandM, z.band);
     ALLOC(c->Lv, z.Lv);
     ALLOC(c->Uv, z.Uv);
+    if (c->precond == 1) {
+        ALLOC(c->ctab, sizeof(double) * 4 * (size_t)g.KP * g.KP);
+        ALLOC(c->clam, sizeof(double) * (size_t)g.n1);
+        ALLOC(c->cdinv, sizeof(double) * (size_t)g.n);
+    }
     if (z.Mkeep) ALLOC(c->Mkeep, z.Mkeep);
     ALLOC(c->order, sizeof(int) * (size_t)g.n);
     ALLOC(c->rowflag, sizeof(unsigned) * (size_t)g.n);
@@ -464,7 +472,7 @@ static int setup_impl(lsg_ctx **out, int d, int N, const int ta[3][3], const int
     if (st != LSG_OK) return fail(st);
     int derr = read_dev_error(c, s);
     if (derr != LSG_OK) return fail(derr);
-    st = build_preconditioner(c, s);
+    st = c->precond == 1 ? build_const_preconditioner(c, s) : build_preconditioner(c, s);
     if (st != LSG_OK) return fail(st);
     release_stage();
     derr = read_dev_error(c, s);
@@ -641,7 +649,8 @@ long long lsg_export_count(lsg_ctx *c, int item)
     case LSG_EXPORT_BAND_S:
     case LSG_EXPORT_BAND_M: return (long long)(g.T + 1) * g.n1 * g.W1;
     case LSG_EXPORT_M: return c->Mkeep ? g.n * g.S : 0;
-    case LSG_EXPORT_LU: return g.n * g.S;
+    case LSG_EXPORT_LU: return c->Lv ? g.n * g.S : 0;
+    case LSG_EXPORT_CONST_EIG: return c->clam ? g.n1 : 0;
     default: return 0;
     }
 }
@@ -658,6 +667,7 @@ int lsg_export(lsg_ctx *c, int item, double *out)
     case LSG_EXPORT_AHAT: src = c->ahat; break;
     case LSG_EXPORT_AHAT_Y: src = c->ahaty; break;
     case LSG_EXPORT_AHAT_Z: src = c->ahatz; break;
+    case LSG_EXPORT_CONST_EIG: src = c->clam; break;
     case LSG_EXPORT_BHAT: src = c->bhat; break;
     case LSG_EXPORT_BAND_S: src = c->bandS; break;
     case LSG_EXPORT_BAND_M: src = c->bandM; break;
@@ -706,6 +716,9 @@ long long lsg_query(lsg_ctx *c, int item)
     case LSG_Q_KX_CALLS: return prof_query(c, PROF_KX, true);
     case LSG_Q_KX_LO_US: return prof_query(c, PROF_KX_LO, false);
     case LSG_Q_KX_LO_CALLS: return prof_query(c, PROF_KX_LO, true);
+    case LSG_Q_CONST_US: return prof_query(c, PROF_CONST, false);
+    case LSG_Q_CONST_CALLS: return prof_query(c, PROF_CONST, true);
+    case LSG_Q_PRECOND_KIND: return c->precond;
     default: return -1;
     }
 }

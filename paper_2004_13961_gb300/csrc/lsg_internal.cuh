@@ -82,7 +82,7 @@ struct PcgGraph {
 };
 
 // stages timed by the optional per-context profiler (LSG_SETUP_PROFILE)
-enum ProfStage : int { PROF_SWEEP_L = 0, PROF_SWEEP_U = 1, PROF_KX = 2, PROF_KX_LO = 3, PROF_STAGES = 4 };
+enum ProfStage : int { PROF_SWEEP_L = 0, PROF_SWEEP_U = 1, PROF_KX = 2, PROF_KX_LO = 3, PROF_CONST = 4, PROF_STAGES = 5 };
 struct Prof;
 
 // reduction scratch: fixed grid so that sums are deterministic
@@ -145,6 +145,11 @@ struct lsg_ctx {
     float t_tables_ms, t_assemble_ms, t_ilu_ms;
     lsg::Prof *prof;           // solve-stage event timing (null unless LSG_SETUP_PROFILE)
     signed char xf_fwd[3], xf_bwd[3];  // tile variant of each FP64 contraction of K x (-1: default)
+    // constant-coefficient preconditioner of PCG-I (LSG_SETUP_CONST_PRECOND) instead of ILU(0)
+    int precond;               // 0: ILU(0) of M, 1: M_0 solved by fast diagonalisation
+    double *ctab;              // parity blocks of E^T (2 x KP^2) then of E (2 x KP^2)
+    double *clam;              // generalised eigenvalues, n1 (index 2k + parity)
+    double *cdinv;             // 1 / D, n
     lsg::PcgGraph *graph;      // the captured FP64 solve (pcg_fp64), built on first use
     int no_graph;              // capture failed once: solves use the host-driven loop
 };
@@ -165,6 +170,8 @@ size_t tc_table_bytes(const Geom &g, int precision);
 int load_vector(lsg_ctx *c, const double *f, double *F, cudaStream_t s);
 int eval_grid(lsg_ctx *c, const double *u, double *vals, cudaStream_t s);
 int apply_Minv(lsg_ctx *c, const double *r, double *z, const int *done, cudaStream_t s);
+int build_const_preconditioner(lsg_ctx *c, cudaStream_t s);
+int apply_const_precond(lsg_ctx *c, const double *r, double *z, const int *done, cudaStream_t s);
 int apply_Minv32(lsg_ctx *c, const float *r, float *z, const int *done, cudaStream_t s);
 int pcg_fp64(lsg_ctx *c, const double *F, double *u, double rtol, int kmax, lsg_info *info,
              cudaStream_t s);

@@ -1567,6 +1567,12 @@ static int sweeps(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done, cud
 // factors with FP64 accumulation.
 int apply_Minv(lsg_ctx *c, const double *r, double *z, const int *done, cudaStream_t s)
 {
+    if (c->precond == 1) {  // PCG-I: the constant-coefficient preconditioner, solved directly
+        int slot;
+        LSG_TRY(prof_begin(c, PROF_CONST, s, &slot));
+        LSG_TRY(apply_const_precond(c, r, z, done, s));
+        return prof_end(c, slot, s);
+    }
     if (c->precision == LSG_FP64) return sweeps<double, double>(c, r, z, c->ys, done, s);
     return sweeps<float, double>(c, r, z, c->ys, done, s);
 }

@@ -46,7 +46,11 @@ constexpr int XT = 256;  // threads per transform CTA
 // axis, length Q).  out[q][b] = sum_k T[q][k] x[b][k] for the term's table T.
 // Tile: TP half-nodes x TB batch columns; 16x16 threads, each RP x RB outputs
 // for the even and the odd half.
-template <typename T, int TP, int TB, int TK>
+// MODE 0: the node-symmetry fold above (outputs at nodes p and Q-1-p).  MODE 1: the
+// tables are parity blocks of a matrix that couples only indices of equal parity (the
+// eigenvector matrices of the constant-coefficient preconditioner): the even half of the
+// input gives output rows 2p, the odd half rows 2p+1 (n1 rows in all).
+template <typename T, int TP, int TB, int TK, int MODE = 0>
 __global__ void __launch_bounds__(XT) k_xf_fwd(const __grid_constant__ XfJob<T> job)
 {
     if (job.done && *job.done) return;
@@ -111,6 +115,20 @@ __global__ void __launch_bounds__(XT) k_xf_fwd(const __grid_constant__ XfJob<T> 
                 }
         }
         __syncthreads();
+    }
+    if (MODE == 1) {
+#pragma unroll
+        for (int i = 0; i < RP; ++i) {
+            const int p = p0 + ty + 16 * i, re = 2 * p, ro = 2 * p + 1;
+#pragma unroll
+            for (int j = 0; j < RB; ++j) {
+                const long long b = b0 + tx + 16 * j;
+                if (b >= B) continue;
+                if (re < n1) O.y[(size_t)re * B + b] = O.scale ? ae[i][j] * O.scale[(size_t)re * B + b] : ae[i][j];
+                if (ro < n1) O.y[(size_t)ro * B + b] = O.scale ? ao[i][j] * O.scale[(size_t)ro * B + b] : ao[i][j];
+            }
+        }
+        return;
     }
     const T sg = tm.tab ? T(-1) : T(1);
     const int Q = job.Q, Qh = job.Qh;
@@ -472,6 +490,54 @@ int eval_grid(lsg_ctx *c, const double *u, double *vals, cudaStream_t s)
     job_init(j, c, Q * Q, nullptr);
     add_out(j, vals, nullptr, Bv, 0);
     return launch_fwd(j, s);
+}
+
+}  // namespace lsg
+
+// ---------------------------------------------------------------------------
+// The constant-coefficient preconditioner of PCG-I (Sec. 5): M_0, the operator with
+// every coefficient replaced by the constant term of its Legendre series, solved
+// directly by fast diagonalisation.  With E the generalised eigenvectors of the 1D
+// mass and stiffness matrices (E^T S E = I, E^T M E = Lambda), E (x) E (x) E turns
+// M_0 into a diagonal D, so z = (E (x) ..)(D^{-1} o ((E^T (x) ..) r)): d contractions
+// with E^T (the last one scaled by 1/D), then d with E.  E couples only indices of
+// equal parity, so each contraction is the parity-split MODE 1 of k_xf_fwd.
+namespace lsg {
+
+int apply_const_precond(lsg_ctx *c, const double *r, double *z, const int *done, cudaStream_t s)
+{
+    const Geom &g = c->g;
+    const long long n1 = g.n1;
+    const size_t blk = (size_t)g.KP * g.KP;
+    const double *Et = c->ctab, *E = c->ctab + 2 * blk;  // [even, odd] halves of E^T, then of E
+    double *buf[2] = {c->ws, c->ws + g.n};
+    const double *in = r;
+    int cur = 0;
+    for (int pass = 0; pass < 2 * g.d; ++pass) {
+        const bool fwd = pass < g.d;
+        const bool last = pass == 2 * g.d - 1;
+        XfJob<double> j;
+        j.nout = 0;
+        j.B = g.n / n1;
+        j.Q = g.Q;
+        j.Qh = (int)((n1 + 1) / 2);
+        j.n1 = (int)n1;
+        j.KP = g.KP;
+        j.tabE[0] = fwd ? Et : E;
+        j.tabO[0] = (fwd ? Et : E) + blk;
+        j.tabE[1] = j.tabE[0];
+        j.tabO[1] = j.tabO[0];
+        j.done = done;
+        double *out = last ? z : buf[cur];
+        add_out(j, out, pass == g.d - 1 ? c->cdinv : nullptr, in, 0);
+        dim3 grid((unsigned)((j.Qh + 15) / 16), (unsigned)((j.B + 31) / 32), 1);
+        ::lsg::count_launch();
+        k_xf_fwd<double, 16, 32, 16, 1><<<grid, XT, 0, s>>>(j);
+        LSG_CK(cudaGetLastError());
+        in = out;
+        cur ^= 1;
+    }
+    return LSG_OK;
 }
 
 }  // namespace lsg

@@ -23,15 +23,17 @@ FP64, MIXED_TF32, MIXED_BF16 = 0, 1, 2
 SETUP_KEEP_M = 1
 SETUP_PROFILE = 2
 SETUP_AUTOTUNE = 4
+SETUP_CONST_PRECOND = 8
 
 EXPORT_GAUSS_X, EXPORT_GAUSS_W, EXPORT_AHAT, EXPORT_BHAT = 0, 1, 2, 3
 EXPORT_BAND_S, EXPORT_BAND_M, EXPORT_M, EXPORT_LU = 4, 5, 6, 7
-EXPORT_AHAT_Y, EXPORT_AHAT_Z = 8, 9
+EXPORT_AHAT_Y, EXPORT_AHAT_Z, EXPORT_CONST_EIG = 8, 9, 10
 
 Q_UNKNOWNS, Q_GRID, Q_HALF_WIDTH, Q_SLOTS, Q_LEVELS, Q_DEVICE_BYTES, Q_NNZ, Q_PRECISION, Q_ASSEMBLE_US, Q_ILU_US = \
     range(10)
 (Q_SWEEP_L_US, Q_SWEEP_L_CALLS, Q_SWEEP_U_US, Q_SWEEP_U_CALLS, Q_KX_US, Q_KX_CALLS, Q_KX_LO_US,
  Q_KX_LO_CALLS) = range(10, 18)
+Q_CONST_US, Q_CONST_CALLS, Q_PRECOND_KIND = 18, 19, 20
 
 OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_ILU_BREAKDOWN, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_NONFINITE = \
     0, -1, -2, -3, -4, -5, -6, -7
@@ -207,7 +209,7 @@ class Context:
     """An lsg_ctx: tables, coefficient samples, M's ILU(0) factors and workspaces."""
 
     def __init__(self, d, N, T, a, b, Q=None, precision=FP64, keep_M=False, stream=None, allow_breakdown=False,
-                 profile=False, autotune=False, ta=None, tb=None):
+                 profile=False, autotune=False, ta=None, tb=None, const_precond=False):
         """A context for lsg_setup_ex (one coefficient a, one degree T), or -- when `a` is a list
         of d per-direction coefficients or the degrees ta (d x d: ta[j][i] of a_j in direction
         i) and tb (d) are given -- for lsg_setup_problem (T unused then)."""
@@ -217,7 +219,8 @@ class Context:
         self.Q = N + 2 if Q is None else Q
         self.precision = precision
         h = ctypes.c_void_p(0)
-        flags = (SETUP_KEEP_M if keep_M else 0) | (SETUP_PROFILE if profile else 0) | (SETUP_AUTOTUNE if autotune else 0)
+        flags = (SETUP_KEEP_M if keep_M else 0) | (SETUP_PROFILE if profile else 0) | (SETUP_AUTOTUNE if autotune else 0) \
+            | (SETUP_CONST_PRECOND if const_precond else 0)
         if isinstance(a, (list, tuple)) or ta is not None or tb is not None:
             alist = list(a) if isinstance(a, (list, tuple)) else [a] * d
             ta = [[T] * d for _ in range(d)] if ta is None else ta

@@ -190,3 +190,59 @@ def test_dir_pcg_matches_dense_solve(d, N):
     assert r["status"] == 0 and r["ilu_status"] == 0
     x = np.linalg.solve(O.dense_K_dir(d, N, Q, a, b), F)
     assert np.abs(r["x"] - x).max() < 1e-11 * np.abs(x).max()
+
+
+# --------------------------------------------------------------------------- PCG-I (Sec. 5)
+
+
+@pytest.mark.parametrize("d,N", [(1, 12), (2, 9), (3, 6)])
+def test_const_preconditioner_is_the_mean_coefficient_operator(d, N):
+    """M_0 (all degrees 0) is the operator with each coefficient replaced by its mean over the
+    square (the constant Legendre term): sum_j mean(beta_j) (M x .. S_j .. x M) + mean(alpha) M^d
+    with S = diag(4k+6) and the pentadiagonal mass matrix; the means by a plain quadrature sum."""
+    Q, n1 = N + 2, N - 1
+    rng = np.random.default_rng(40 + d)
+    g = _grid(d, Q)
+    a = [np.exp(0.5 * np.sin(1.0 + j + g[j]) + 0.2 * g[-1]) for j in range(d)]
+    b = 1.0 + 0.3 * np.cos(sum(g))
+    x, w = np.polynomial.legendre.leggauss(Q)
+    Wt = np.ones(1)
+    for _ in range(d):
+        Wt = np.kron(w, Wt)
+    mean = lambda v: float(Wt @ v) / 2 ** d
+    S, M = np.diag(4.0 * np.arange(n1) + 6.0), _mass_1d(n1)
+
+    def kron(mats):
+        out = np.ones((1, 1))
+        for m in reversed(mats):
+            out = np.kron(out, m)
+        return out
+
+    ref = sum(mean(a[j]) * kron([S if i == j else M for i in range(d)]) for j in range(d)) + mean(b) * kron([M] * d)
+    st = O.setup_const(d, N, Q, a, b)
+    assert np.abs(st["dense"] - ref).max() < 1e-13 * np.abs(ref).max()
+    assert abs(st["abar"][0] - mean(a[0])) < 1e-14 * abs(mean(a[0]))
+
+
+def test_const_preconditioner_exact_for_constant_coefficients():
+    """Constant coefficients: M_0 = K, so PCG-I converges in one iteration."""
+    d, N, Q = 2, 12, 14
+    nq = Q ** d
+    a, b = [np.full(nq, 1.7), np.full(nq, 0.6)], np.full(nq, 2.5)
+    F = np.random.default_rng(2).standard_normal((N - 1) ** d)
+    r = O.pcg_const(d, N, Q, a, b, F, eps=1e-12)
+    assert r["status"] == 0 and r["iters"] == 1
+    assert np.abs(r["setup"]["dense"] - O.dense_K_dir(d, N, Q, a, b)).max() < 1e-12
+
+
+@pytest.mark.parametrize("d,N", [(2, 10), (3, 6)])
+def test_const_pcg_matches_dense_solve(d, N):
+    Q = N + 1
+    g = _grid(d, Q)
+    a = [np.exp(g[j]) for j in range(d)]
+    b = np.cos(sum(g))
+    F = np.random.default_rng(5).standard_normal((N - 1) ** d)
+    r = O.pcg_const(d, N, Q, a, b, F, eps=1e-13)
+    assert r["status"] == 0
+    x = np.linalg.solve(O.dense_K_dir(d, N, Q, a, b), F)
+    assert np.abs(r["x"] - x).max() < 1e-11 * np.abs(x).max()
