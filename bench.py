@@ -633,7 +633,9 @@ def run_profile_case(args):
     prec = {"n256-fp64": lsg.FP64, "n256-tf32": lsg.MIXED_TF32, "n256-bf16": lsg.MIXED_BF16}[args.profile_case]
     p = W.random_exp_problem(2, 256, 8, 1, 2, 3)
     a, b, f = (torch.tensor(p[k], device=dev) for k in ("a", "b", "f"))
-    ctx = lsg.Context(2, 256, 8, a, b, precision=prec)
+    # profiled context: the host-driven PCG loop (kernels inside a graph's device-side loop
+    # cannot be captured one by one)
+    ctx = lsg.Context(2, 256, 8, a, b, precision=prec, profile=True)
     F = ctx.load_vector(f)
     u, info = ctx.pcg_solve(F, rtol=1e-12 if prec == lsg.FP64 else 1e-10)
     torch.cuda.synchronize()
