@@ -63,7 +63,7 @@ __global__ void k_const_blocks(int n1, int w, int W1, const double *bandM, doubl
 // One thread per eigenpair (parity p, index k in ascending order of the block's
 // eigenvalues).  Writes lam[2k+p] and the eigenvector's tables: the parity blocks of
 // E^T (rows: eigen index, columns: basis index) and of E (the transposes), each
-// KP x KP with zero padding, E = S^{-1/2} Y.  scratch: 5 m doubles per thread.
+// KP x KP with zero padding, E = S^{-1/2} Y.  scratch: 5 ceil(n1/2) doubles per thread.
 __global__ void k_const_eig(int n1, int KP, const double *a, const double *e, const double *e2, double *lam,
                             double *tab, double *scratch, int *err)
 {
@@ -91,7 +91,8 @@ __global__ void k_const_eig(int n1, int KP, const double *a, const double *e, co
     const double lamk = 0.5 * (lo + hi);
     lam[2 * k + p] = lamk;
     // inverse iteration: (A - lam) y = v, partial pivoting on the tridiagonal
-    double *dl = scratch + (size_t)t * 5 * m, *dd = dl + m, *du = dd + m, *du2 = du + m, *y = du2 + m;
+    // per-thread scratch at a fixed stride (the two parity blocks differ in size when n1 is odd)
+    double *dl = scratch + (size_t)t * 5 * half, *dd = dl + m, *du = dd + m, *du2 = du + m, *y = du2 + m;
     const double shift = lamk + 1e-15 * fmax(fabs(lamk), 1e-300);
     for (int r = 0; r < m; ++r) y[r] = 1.0 + 0.01 * (double)((r * 7 + k * 3) % 11);
     for (int iter = 0; iter < 3; ++iter) {

@@ -619,14 +619,8 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
 //     finisher stores each value.  The output is filled with a signalling NaN
 //     before the sweep and every value is stored once, so a word that differs
 //     from the fill is final: no progress words, no fences.  (Arithmetic never
-//     produces a signalling NaN.)
-// In 3D the newest dependencies of a row also come from the previous plane: line
-// (j + dy_p, k - 1), dy_p = min(w, n1-1-j) in sweep order, holds values at the same
-// wavefront levels as the previous line of the row's own plane (L-1 .. L-K for the
-// K newest).  The near loader stages that line too, and the finisher applies its K
-// newest values to the window like the previous line's, so the stale part never
-// waits for a value produced one level earlier; the stale warps read the older
-// lines of the other planes from the output through L1.
+//     produces a signalling NaN.)  In 3D the stale warps read the other planes'
+//     values from the output the same way, through L1.
 // Lines are claimed in sweep order, so a CTA only waits for lines claimed
 // earlier by running CTAs; every wait is bounded and reports LSG_ERR_TIMEOUT.
 constexpr int L1_NS = 6;                 // stale warps
@@ -728,7 +722,7 @@ __global__ void k_line_fill(AT *out, long long n, unsigned *counter, const int *
 
 struct LineSmem {
     size_t sy, srhs, sT, ring, mbar, meta, tab, total;
-    int RS, PADL, rows;  // row stride, left padding (elements), value rows (halo, own line, 3D: plane line)
+    int RS, PADL, rows;  // row stride, left padding (elements), value rows (halo + own line)
 };
 
 __host__ __device__ inline LineSmem line_layout(int d, int n1, int w, int D, int RL, int vsize, int nslot, int asize)
@@ -736,7 +730,7 @@ __host__ __device__ inline LineSmem line_layout(int d, int n1, int w, int D, int
     LineSmem L;
     L.PADL = (w + 1) / 2 * 2;                 // positions -w .. -1 (even: 16-byte row starts)
     L.RS = (L.PADL + n1 + w + 1) / 2 * 2;     // ... n1 .. n1+w-1 on the right
-    L.rows = d == 3 ? w + 2 : d == 2 ? w + 1 : 1;  // 3D: plus the previous plane's newest line
+    L.rows = d >= 2 ? w + 1 : 1;
     size_t o = 0;
     L.sy = o;   o += (size_t)L.rows * L.RS * asize;
     L.srhs = o; o += (size_t)n1 * asize;
@@ -842,16 +836,14 @@ __device__ __forceinline__ bool poll_global(const AT *p, AT &val, const volatile
 // line's value until both are final.  Kept out of line so that the step loop
 // holds no loop of its own.
 template <typename AT>
-__device__ __noinline__ bool poll_operands(const AT *pT, const AT *pP, const AT *pL, AT *Tv, AT *yp, AT *yl,
-                                           const volatile int *abort_flag, int *err, long long budget)
+__device__ __noinline__ bool poll_operands(const AT *pT, const AT *pP, AT *Tv, AT *yp, const volatile int *abort_flag,
+                                           int *err, long long budget)
 {
-    AT a, b = AT(0), c = AT(0);
-    const bool good = poll_value(pT, a, abort_flag, err, budget) &&
-                      (pP == nullptr || poll_value(pP, b, abort_flag, err, budget)) &&
-                      (pL == nullptr || poll_value(pL, c, abort_flag, err, budget));
+    AT a, b = AT(0);
+    const bool good =
+        poll_value(pT, a, abort_flag, err, budget) && (pP == nullptr || poll_value(pP, b, abort_flag, err, budget));
     *Tv = a;
     if (pP != nullptr) *yp = b;
-    if (pL != nullptr) *yl = c;
     return good;
 }
 
@@ -887,9 +879,7 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
     const int n1 = G.n1, w = G.w, RL = A.RL, nslot = G.Sc, K = A.K;
     extern __shared__ __align__(128) unsigned char smem[];
     const LineSmem Lo = line_layout(G.d, n1, w, D, RL, (int)sizeof(V), nslot, (int)sizeof(AT));
-    // value row of the own line; row own-h: line v-h; 3D: row own+1 holds the previous plane's line
-    const int RS = Lo.RS, PADL = Lo.PADL, own = G.d == 3 ? Lo.rows - 2 : Lo.rows - 1;
-    const int plrow = own + 1;
+    const int RS = Lo.RS, PADL = Lo.PADL, own = Lo.rows - 1;  // value row of the own line; row own-h: line v-h
     AT *sy = (AT *)(smem + Lo.sy);
     AT *srhs = (AT *)(smem + Lo.srhs);
     AT *sT = (AT *)(smem + Lo.sT);
@@ -900,9 +890,7 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
     __shared__ volatile int s_prog;            // positions the finisher completed
     __shared__ volatile int s_near, s_near2;   // positions of lines v-1 and v-2 staged in shared memory
     __shared__ volatile int s_far;             // ... of lines v-3 .. v-w (minimum)
-    __shared__ volatile int s_pl;              // 3D: ... of the previous plane's line (dy_p, -1)
     __shared__ int s_fown[32], s_fprev[32];    // slots of the window's fresh terms (lane j)
-    __shared__ int s_fpl[32];                  // 3D: ... of the previous plane's line (per line)
     __shared__ long long s_line;
     __shared__ int s_issued;                   // chunks the producer issued (this line)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -978,7 +966,6 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
             s_near = 0;
             s_near2 = 0;
             s_far = 0;
-            s_pl = 0;
             s_issued = 0;
             s_abort = (*(volatile int *)A.err != 0) ? 1 : 0;
         }
@@ -992,28 +979,10 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
         // no neighbours of this one (3D) and are neither staged nor waited for
         const long long vin = G.d == 3 ? v % n1 : v;
         const bool prev_exists = G.d >= 2 && vin >= 1;
-        // 3D: in sweep order, the newest dependencies of a row in the previous plane lie on
-        // line (j + dy_p, k - 1), dy_p = min(w, n1-1-j), at the same positions as those of
-        // the previous line of its own plane (levels L-1 .. L-K for the K newest); its
-        // values reach the finisher's window through a shared row like line v-1's
-        const bool pl_exists = G.d == 3 && v >= n1;
-        const int dyp = G.d == 3 ? min(w, n1 - 1 - (int)vin) : 0;
-        const long long vpl = v - n1 + dyp;  // its index in sweep order
         bits_t *ybits = reinterpret_cast<bits_t *>(sy);
         for (int e = threadIdx.x; e < Lo.rows * RS; e += blockDim.x) {
             const int r = e / RS, c = e - r * RS - PADL;
-            const bool fresh = c >= 0 && c < n1 && ((prev_exists && r == own - 1) || (pl_exists && r == plrow));
-            ybits[e] = fresh ? FB::v : bits_t(0);
-        }
-        if (threadIdx.x < 32) {
-            // the window slot of the plane line for lane j: offset (DIR (w-j), DIR dy_p, -DIR)
-            const int jj = threadIdx.x, dx = DIR * (w - jj);
-            int t = -1;
-            if (G.d == 3 && jj < K && jj <= 2 * w) {
-                const int sl = slot_index(G, dx, DIR * dyp, -DIR);
-                t = DIR > 0 ? sl : sl - (G.Sc + 1);
-            }
-            s_fpl[jj] = t;
+            ybits[e] = (prev_exists && r == own - 1 && c >= 0 && c < n1) ? FB::v : bits_t(0);
         }
         for (int e = threadIdx.x; e < L1_DT; e += blockDim.x) reinterpret_cast<bits_t *>(sT)[e] = FB::v;
         for (int q = threadIdx.x; q < n1; q += blockDim.x) srhs[q] = rhs[q + (long long)n1 * line];
@@ -1029,17 +998,13 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
                 const unsigned m = meta[t];
                 const int dx = (int)(m & 255u) - 128, dy = (int)((m >> 8) & 255u) - 128, dz = (int)((m >> 16) & 255u) - 128;
                 const int om = -DIR * dx, oj = w - DIR * dx;
-                const bool plane = dz == -DIR && dy == DIR * dyp;  // the previous plane's staged line
-                const bool win = (dz == 0 && ((dy == 0 && om >= 1 && om <= K) || (dy == -DIR && oj >= 0 && oj < K))) ||
-                                 (plane && oj >= 0 && oj < K);
+                const bool win = dz == 0 && ((dy == 0 && om >= 1 && om <= K) || (dy == -DIR && oj >= 0 && oj < K));
                 const int cj = lj + dy, ck = lk + dz;
                 int2 e;
                 if (win || cj < 0 || cj >= n1 || ck < 0 || ck >= n1) {
                     e = make_int2(0, -1);
                 } else if (dz == 0) {
                     e = make_int2((own + DIR * dy) * RS + PADL + dx, (dx + 64) | (1 << 8));
-                } else if (plane) {
-                    e = make_int2(plrow * RS + PADL + dx, (dx + 64) | (1 << 8));
                 } else {
                     e = make_int2(dx + n1 * (dy + n1 * dz), dx + 64);
                 }
@@ -1051,7 +1016,6 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
             if (G.d < 2 || vin < 1) s_near = n1;
             if (G.d < 2 || vin < 2) s_near2 = n1;
             if (G.d < 2 || vin < 3 || w < 3) s_far = n1;
-            if (!pl_exists) s_pl = n1;
         }
         __syncthreads();
         bool ok = true;
@@ -1060,10 +1024,8 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
             // ---------------------------------------------------------------- finisher
             const int j = lane;
             const int fo_t = j < K ? s_fown[j] : -1, fp_t = j < K ? s_fprev[j] : -1;
-            const int fl_t = (j < K && pl_exists) ? s_fpl[j] : -1;
             const int myrow = own * RS + PADL;
             const int prevoff = G.d >= 2 ? (own - 1) * RS + PADL + DIR * w : 0;
-            const int ploff = plrow * RS + PADL + DIR * w;  // 3D: the previous plane's line, at position 0
             // lane j holds Gw, the fresh part of position s+j so far; yb = y_{s-1}.  The
             // window starts K-1 steps before position 0 so that every position receives
             // its K newest previous-line values here (steps s < 0 only apply those).
@@ -1074,24 +1036,21 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
             // their latency overlaps the shuffles: the window's factors, the stale part
             // and the previous line's value (zero past the line's ends; both are final
             // once they differ from the fill)
-            AT fo = 0, fp = 0, fl = 0, ri = 1;
+            AT fo = 0, fp = 0, ri = 1;
             // shared addresses: this lane's factor slots in ring row 0, the stale ring,
             // the previous line's row (at position 0) and the own row
             const unsigned a_ring = smem_u32(ring) + (unsigned)((DIR > 0 ? 0 : 1) * (int)sizeof(V));
             const unsigned a_fo = a_ring + (unsigned)(max(fo_t, 0) * (int)sizeof(V));
             const unsigned a_fp = a_ring + (unsigned)(max(fp_t, 0) * (int)sizeof(V));
-            const unsigned a_fl = a_ring + (unsigned)(max(fl_t, 0) * (int)sizeof(V));
             const unsigned a_ri = a_ring + (unsigned)((RL - 2) * (int)sizeof(V));
             const unsigned rowb = (unsigned)(RL * (int)sizeof(V));
             const unsigned a_T = smem_u32(sT), a_P = smem_u32(sy + prevoff), a_Y = smem_u32(sy + myrow);
-            const unsigned a_L = smem_u32(sy + ploff);
             auto load_factors = [&](int s) {
                 const int qj = s + j;
                 const bool in = j < K && qj >= 0 && qj < n1;
                 const unsigned ro = (unsigned)(qj & (D - 1)) * rowb;
                 fo = (in && fo_t >= 0) ? (AT)lds_val(a_fo + ro, V(0)) : AT(0);
                 fp = (in && fp_t >= 0) ? (AT)lds_val(a_fp + ro, V(0)) : AT(0);
-                if (G.d == 3) fl = (in && fl_t >= 0) ? (AT)lds_val(a_fl + ro, V(0)) : AT(0);
                 if (DIR < 0) ri = in ? (AT)lds_val(a_ri + ro, V(0)) : AT(1);  // 1 / U(i,i), stored by the factorisation
             };
             auto load_T = [&](int s) -> bits_t {
@@ -1102,19 +1061,11 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
                            ? lds_vol(a_P + (unsigned)((DIR > 0 ? s : n1 - 1 - s) * (int)sizeof(AT)), bits_t(0))
                            : bits_t(0);
             };
-            auto load_L = [&](int s) -> bits_t {
-                return (G.d == 3 && s + w >= 0)
-                           ? lds_vol(a_L + (unsigned)((DIR > 0 ? s : n1 - 1 - s) * (int)sizeof(AT)), bits_t(0))
-                           : bits_t(0);
-            };
-            bits_t tb = 0, pb = 0, lb = 0;
-            // the window's factors, the stale part, the previous line's value (and, 3D, the
-            // previous plane's line's value)
-            auto next_operands = [&](int s) {
+            bits_t tb = 0, pb = 0;
+            auto next_operands = [&](int s) {  // the window's factors, the stale part, the previous line's value
                 load_factors(s);
                 tb = load_T(s);
                 pb = load_P(s);
-                if (G.d == 3) lb = load_L(s);
             };
             // ring chunks the finisher has waited for: rows [0, rows_ok) have landed
             int rows_ok = 0;
@@ -1131,12 +1082,10 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
             ok = ok && need_rows(K);
             if (ok) next_operands(s0);
             for (int s = s0; s < 0 && ok; ++s) {
-                AT yp = FB::val(pb), yl = FB::val(lb);
+                AT yp = FB::val(pb);
                 if (pb == FB::v) ok = poll_value(&sy[prevoff + (DIR > 0 ? s : n1 - 1 - s)], yp, &s_abort, A.err, A.budget);
-                if (ok && G.d == 3 && lb == FB::v)
-                    ok = poll_value(&sy[ploff + (DIR > 0 ? s : n1 - 1 - s)], yl, &s_abort, A.err, A.budget);
                 if (!ok) break;
-                const AT r = G.d == 3 ? fma(-fp, yp, fma(-fl, yl, Gw)) : fma(-fp, yp, Gw);
+                const AT r = fma(-fp, yp, Gw);
                 Gw = __shfl_down_sync(FULL, r, 1);
                 if (j >= K - 1) Gw = AT(0);
                 next_operands(s + 1);
@@ -1146,15 +1095,13 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
             // an operand that is not final yet (rare) is polled outside the hot loop's code
             AT Bv = 0;
             auto make_B = [&](int s) -> bool {
-                AT Tv = FB::val(tb), yp = FB::val(pb), yl = FB::val(lb);
-                if (__any_sync(FULL, tb == FB::v || pb == FB::v || (G.d == 3 && lb == FB::v))) {
-                    const int is = DIR > 0 ? s : n1 - 1 - s;
-                    if (!poll_operands(&sT[s % L1_DT], G.d >= 2 ? &sy[prevoff + is] : nullptr,
-                                       G.d == 3 ? &sy[ploff + is] : nullptr, &Tv, &yp, &yl, &s_abort, A.err, A.budget))
+                AT Tv = FB::val(tb), yp = FB::val(pb);
+                if (__any_sync(FULL, tb == FB::v || pb == FB::v)) {
+                    if (!poll_operands(&sT[s % L1_DT], G.d >= 2 ? &sy[prevoff + (DIR > 0 ? s : n1 - 1 - s)] : nullptr,
+                                       &Tv, &yp, &s_abort, A.err, A.budget))
                         return false;
                 }
-                const AT t0 = (j == 0) ? Tv : AT(0);
-                Bv = G.d == 3 ? fma(-fp, yp, fma(-fl, yl, t0)) : fma(-fp, yp, t0);
+                Bv = fma(-fp, yp, (j == 0) ? Tv : AT(0));
                 return true;
             };
             if (ok && n1 > 0) ok = make_B(0);
@@ -1196,7 +1143,6 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
             for (int q = sw; q < n1 && ok; q += L1_NS) {
                 ok = wait_ge(&s_prog, q - K, &s_abort, A.err, A.budget) &&
                      wait_ge(&s_near, min(max(0, q + w - K + 1), n1), &s_abort, A.err, A.budget) &&
-                     (G.d < 3 || wait_ge(&s_pl, min(max(0, q + w - K + 1), n1), &s_abort, A.err, A.budget)) &&
                      wait_ge(&s_near2, min(q + w + 1, n1), &s_abort, A.err, A.budget) &&
                      wait_ge(&s_far, min(q + w + 1, n1), &s_abort, A.err, A.budget) && wait_chunk(it, q);
                 if (!ok) break;
@@ -1323,42 +1269,33 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
             }
         } else if (role == R_NEAR) {
             // ---------------------------------------------------------------- loader: lines v-1, v-2
-            // (3D: and the previous plane's line); 32 positions of each line per poll; the staged
-            // prefix is what differs from the fill
-            int b1 = s_near, b2 = s_near2, b3 = s_pl;
+            // 32 positions of each line per poll; the staged prefix is what differs from the fill
+            int b1 = s_near, b2 = s_near2;
             const long long l1 = DIR > 0 ? v - 1 : G.nlines - v;
             const long long l2 = DIR > 0 ? v - 2 : G.nlines + 1 - v;
-            const long long l3 = DIR > 0 ? vpl : G.nlines - 1 - vpl;
-            AT *r1 = sy + (own - 1) * RS + PADL, *r2 = sy + (own - 2) * RS + PADL, *r3 = sy + plrow * RS + PADL;
+            AT *r1 = sy + (own - 1) * RS + PADL, *r2 = sy + (own - 2) * RS + PADL;
             const long long t0 = clock64();
-            for (int itp = 0; b1 < n1 || b2 < n1 || b3 < n1; ++itp) {
-                const int p1 = b1 + lane, p2 = b2 + lane, p3 = b3 + lane;
+            for (int itp = 0; b1 < n1 || b2 < n1; ++itp) {
+                const int p1 = b1 + lane, p2 = b2 + lane;
                 const int i1 = DIR > 0 ? p1 : n1 - 1 - p1, i2 = DIR > 0 ? p2 : n1 - 1 - p2;
-                const int i3 = DIR > 0 ? p3 : n1 - 1 - p3;
-                bits_t x1 = FB::v, x2 = FB::v, x3 = FB::v;
+                bits_t x1 = FB::v, x2 = FB::v;
                 if (p1 < n1) x1 = ld_poll(out + l1 * n1 + i1);
                 if (p2 < n1) x2 = ld_poll(out + l2 * n1 + i2);
-                if (p3 < n1) x3 = ld_poll(out + l3 * n1 + i3);
                 const unsigned m1 = __ballot_sync(FULL, p1 < n1 && x1 != FB::v);
                 const unsigned m2 = __ballot_sync(FULL, p2 < n1 && x2 != FB::v);
-                const unsigned m3 = __ballot_sync(FULL, p3 < n1 && x3 != FB::v);
                 const int c1 = m1 == FULL ? 32 : __ffs(~m1) - 1;
                 const int c2 = m2 == FULL ? 32 : __ffs(~m2) - 1;
-                const int c3 = m3 == FULL ? 32 : __ffs(~m3) - 1;
                 if (lane < c1) r1[i1] = FB::val(x1);
                 if (lane < c2) r2[i2] = FB::val(x2);
-                if (lane < c3) r3[i3] = FB::val(x3);
-                if (c1 + c2 + c3 > 0) {
+                if (c1 + c2 > 0) {
                     __syncwarp();
                     if (lane == 0) {
                         __threadfence_block();
-                        if (c3) st_release_cta(&s_pl, b3 + c3);
                         if (c2) st_release_cta(&s_near2, b2 + c2);
                         if (c1) st_release_cta(&s_near, b1 + c1);
                     }
                     b1 += c1;
                     b2 += c2;
-                    b3 += c3;
                 } else {
                     if (itp > 64) __nanosleep(32);
                     if ((itp & 15) == 15) {
