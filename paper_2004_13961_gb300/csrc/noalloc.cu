@@ -39,7 +39,11 @@ extern "C" int lsg_gauss_noalloc(int Q, double *x, double *w)
     }
     int dev = 0;
     LSG_CK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return LSG_ERR_ARG;
+    if (dev < 0 || dev >= kMaxDevices) {
+        lsg::record_cuda_error(cudaErrorInvalidDevice, "lsg_gauss_noalloc: device index beyond the 64 devices it keeps a scratch address for",
+                               __FILE__, __LINE__);
+        return LSG_ERR_ARG;
+    }
     double *base = nullptr;
     {
         // once per device, with that device current: the host-side symbol is only a

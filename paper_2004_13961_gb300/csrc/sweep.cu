@@ -164,6 +164,45 @@ __device__ __forceinline__ void st_release_cta(volatile int *p, int v)
     asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(smem_u32((const void *)p)), "r"(v) : "memory");
 }
 
+// Thread-block clusters: the 2D line sweep hands each finished value to the CTA of
+// the next line through distributed shared memory.
+__device__ __forceinline__ unsigned cluster_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_size()
+{
+    unsigned n;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+    return n;
+}
+// every thread of every CTA of the cluster arrives; memory before it is visible after it
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// the shared::cluster address of this CTA's shared address `a` in CTA `rank` of the cluster
+__device__ __forceinline__ unsigned cluster_map(unsigned a, unsigned rank)
+{
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster(unsigned a, double v)
+{
+    asm volatile("st.relaxed.cluster.shared::cluster.b64 [%0], %1;" ::"r"(a), "l"(__double_as_longlong(v)) : "memory");
+}
+__device__ __forceinline__ void st_cluster(unsigned a, float v)
+{
+    asm volatile("st.relaxed.cluster.shared::cluster.b32 [%0], %1;" ::"r"(a), "r"(__float_as_uint(v)) : "memory");
+}
+__device__ __forceinline__ void st_cluster_u64(unsigned a, unsigned long long v)
+{
+    asm volatile("st.relaxed.cluster.shared::cluster.b64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+
 // Bounded spin until a shared counter reaches `need`: tight polls first (the
 // producer is a warp of this CTA a few hundred cycles away), then sleeps.
 __device__ __forceinline__ bool wait_count(const volatile int *c, int need, const volatile int *abort_flag, int *err,
@@ -625,7 +664,8 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
 // earlier by running CTAs; every wait is bounded and reports LSG_ERR_TIMEOUT.
 constexpr int L1_NS = 6;                 // stale warps
 constexpr int L1_DT = 32;                // ring of stale results (positions)
-constexpr int L1_WARPS = 11;             // finisher, six stale warps, TMA producer, two loaders, one idle
+constexpr int L1_WARPS = 12;             // finisher, six stale warps, TMA producer, two loaders, two idle
+constexpr int L1_CLUSTER = 8;            // 2D: lines per cluster group (one per CTA)
 constexpr int L1_D = 32;                 // factor ring depth (rows); rows D further ahead are prefetched to L2
 constexpr int L1_CH = 4;                 // rows per ring barrier (the finisher checks one per L1_CH positions)
 constexpr int L1_DS = 8;                 // ring depth where 32 rows do not fit (3D rows)
@@ -893,13 +933,21 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
     __shared__ int s_fown[32], s_fprev[32];    // slots of the window's fresh terms (lane j)
     __shared__ long long s_line;
     __shared__ int s_issued;                   // chunks the producer issued (this line)
+    __shared__ unsigned long long s_group;     // cluster mode: the group rank 0 claimed (all ones: stop)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // warp roles (warp w runs on SM sub-partition w % 4): the finisher on
-    // sub-partition 0 with only the far loader (mostly idle) and an idle warp; the
-    // stale warps two per sub-partition 1-3 with the producer and the near loader
+    // warp roles (warp w runs on SM sub-partition w % 4): the finisher alone on
+    // sub-partition 0 (with two idle warps); the stale warps two per sub-partition 1-3,
+    // with the producer, the near loader and the far loader one each (the far loader
+    // polls up to eight lines without pause: beside the finisher it slowed the
+    // backward sweep's step by 12 %)
     enum { R_FIN, R_STALE, R_PROD, R_NEAR, R_FAR, R_IDLE };
-    const int role = wid == 0 ? R_FIN : wid == 4 ? R_FAR : wid == 8 ? R_IDLE : wid == 9 ? R_PROD : wid == 10 ? R_NEAR
-                                                                                                            : R_STALE;
+    const int role = wid == 0 ? R_FIN : (wid == 4 || wid == 8) ? R_IDLE : wid == 9 ? R_PROD : wid == 10 ? R_NEAR
+                   : wid == 11 ? R_FAR : R_STALE;
+    // cluster mode (2D, launched in clusters): CTA `crank` of a cluster takes line
+    // csz g + crank of the group g that rank 0 claims, and stores each value it finishes
+    // into the previous-line row of CTA crank + 1 as well
+    const unsigned csz = cluster_size(), crank = cluster_rank();
+    const bool clu = csz > 1;
     const int sw = wid < 4 ? wid - 1 : wid - 2;  // stale warp index (R_STALE)
     const AT *rhs = (const AT *)A.rhs;
     AT *out = (AT *)A.out;
@@ -958,10 +1006,23 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
         }
     }
 
-    for (int it = 0;; ++it) {
+    for (int it = 0;;) {
         __syncthreads();
+        if (clu) {
+            // every CTA of the cluster is done with the previous group, so none stores into
+            // another's rows any more; rank 0 claims the next group for all (stop: past the
+            // last line, or an error anywhere)
+            cluster_sync_all();
+            if (crank == 0 && threadIdx.x == 0) {
+                const unsigned long long g = atomicAdd(A.counter, 1u);
+                const bool stop = (long long)g * csz >= G.nlines || *(volatile int *)A.err != 0;
+                for (unsigned r = 0; r < csz; ++r) st_cluster_u64(cluster_map(smem_u32(&s_group), r), stop ? ~0ull : g);
+            }
+            cluster_sync_all();
+            if (s_group == ~0ull) return;  // all CTAs of the cluster alike; nothing in flight
+        }
         if (threadIdx.x == 0) {
-            s_line = atomicAdd(A.counter, 1u);
+            s_line = clu ? (long long)s_group * csz + crank : (long long)atomicAdd(A.counter, 1u);
             s_prog = 0;
             s_near = 0;
             s_near2 = 0;
@@ -971,7 +1032,9 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
         }
         __syncthreads();
         const long long v = s_line;
-        if (v >= G.nlines || s_abort) return;  // no copy is in flight between lines
+        if (!clu && (v >= G.nlines || s_abort)) return;  // no copy is in flight between lines
+        // cluster mode: a CTA past the last line sits the group out (the next claim stops)
+        const bool live = v < G.nlines && !s_abort;
         const long long line = DIR > 0 ? v : G.nlines - 1 - v;
         // the finisher polls the values of line v-1 and the stale results for the
         // fill pattern; everything else starts at zero (padding, absent lines)
@@ -985,7 +1048,8 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
             ybits[e] = (prev_exists && r == own - 1 && c >= 0 && c < n1) ? FB::v : bits_t(0);
         }
         for (int e = threadIdx.x; e < L1_DT; e += blockDim.x) reinterpret_cast<bits_t *>(sT)[e] = FB::v;
-        for (int q = threadIdx.x; q < n1; q += blockDim.x) srhs[q] = rhs[q + (long long)n1 * line];
+        if (live)
+            for (int q = threadIdx.x; q < n1; q += blockDim.x) srhs[q] = rhs[q + (long long)n1 * line];
         if (G.d == 3) {
             // the line's slot table: each slot of the stale part that can be in the grid
             // for some position, with the offset of its value from position i (in the
@@ -1017,10 +1081,16 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
             if (G.d < 2 || vin < 2) s_near2 = n1;
             if (G.d < 2 || vin < 3 || w < 3) s_far = n1;
         }
-        __syncthreads();
+        // cluster mode: every row is filled before a neighbour stores into it
+        if (clu)
+            cluster_sync_all();
+        else
+            __syncthreads();
         bool ok = true;
 
-        if (role == R_FIN) {
+        if (!live) {
+            // past the last line (cluster mode): nothing to do in this group
+        } else if (role == R_FIN) {
             // ---------------------------------------------------------------- finisher
             const int j = lane;
             const int fo_t = j < K ? s_fown[j] : -1, fp_t = j < K ? s_fprev[j] : -1;
@@ -1045,6 +1115,10 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
             const unsigned a_ri = a_ring + (unsigned)((RL - 2) * (int)sizeof(V));
             const unsigned rowb = (unsigned)(RL * (int)sizeof(V));
             const unsigned a_T = smem_u32(sT), a_P = smem_u32(sy + prevoff), a_Y = smem_u32(sy + myrow);
+            // cluster mode: the next line's CTA reads this line's values from its own
+            // previous-line row, which lane 0 fills as well
+            const bool fwd = clu && crank + 1 < csz && v + 1 < G.nlines;
+            const unsigned a_next = fwd ? cluster_map(smem_u32(sy + (own - 1) * RS + PADL), crank + 1) : 0u;
             auto load_factors = [&](int s) {
                 const int qj = s + j;
                 const bool in = j < K && qj >= 0 && qj < n1;
@@ -1131,7 +1205,10 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
                     st_release_cta(&s_prog, s + 1);
                     // and to the output for the next lines (after the release: its fence does
                     // not wait for this store)
-                    if (lane == 0) st_final(out + i + (long long)n1 * line, yb);
+                    if (lane == 0) {
+                        if (fwd) st_cluster(a_next + (unsigned)(i * (int)sizeof(AT)), yb);
+                        st_final(out + i + (long long)n1 * line, yb);
+                    }
                     if (more) ok = make_B(s + 1);
                 }
             }
@@ -1274,18 +1351,21 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
             const long long l1 = DIR > 0 ? v - 1 : G.nlines - v;
             const long long l2 = DIR > 0 ? v - 2 : G.nlines + 1 - v;
             AT *r1 = sy + (own - 1) * RS + PADL, *r2 = sy + (own - 2) * RS + PADL;
+            // cluster mode, rank > 0: line v-1's CTA stores its values into row r1 itself;
+            // the loader only follows how far it is final (for the stale warps)
+            const bool local1 = clu && crank > 0;
             const long long t0 = clock64();
             for (int itp = 0; b1 < n1 || b2 < n1; ++itp) {
                 const int p1 = b1 + lane, p2 = b2 + lane;
                 const int i1 = DIR > 0 ? p1 : n1 - 1 - p1, i2 = DIR > 0 ? p2 : n1 - 1 - p2;
                 bits_t x1 = FB::v, x2 = FB::v;
-                if (p1 < n1) x1 = ld_poll(out + l1 * n1 + i1);
+                if (p1 < n1) x1 = local1 ? lds_vol(smem_u32(r1 + i1), bits_t(0)) : ld_poll(out + l1 * n1 + i1);
                 if (p2 < n1) x2 = ld_poll(out + l2 * n1 + i2);
                 const unsigned m1 = __ballot_sync(FULL, p1 < n1 && x1 != FB::v);
                 const unsigned m2 = __ballot_sync(FULL, p2 < n1 && x2 != FB::v);
                 const int c1 = m1 == FULL ? 32 : __ffs(~m1) - 1;
                 const int c2 = m2 == FULL ? 32 : __ffs(~m2) - 1;
-                if (lane < c1) r1[i1] = FB::val(x1);
+                if (lane < c1 && !local1) r1[i1] = FB::val(x1);
                 if (lane < c2) r2[i2] = FB::val(x2);
                 if (c1 + c2 > 0) {
                     __syncwarp();
@@ -1373,7 +1453,7 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
         }
         if (!ok && lane == 0) s_abort = 1;
         __syncthreads();
-        if (s_abort) {
+        if (live && s_abort) {
             // the last chunk issued on each ring barrier must land before the CTA exits
             if (threadIdx.x == 0) {
                 const int iss = s_issued;
@@ -1381,9 +1461,13 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
                     const int cl = b + ((iss - 1 - b) / NB) * NB;
                     mbar_wait(&mbar[b], parity(it, cl * L1_CH), A.err);
                 }
+                // cluster mode: the next claim stops every cluster (an abort follows a
+                // recorded error; this keeps the first one)
+                if (clu) set_err(A.err, DERR_TIMEOUT);
             }
-            return;
+            if (!clu) return;
         }
+        if (live) ++it;  // the ring barriers' phases count the lines this CTA swept
     }
 }
 
@@ -1409,7 +1493,7 @@ static int launch_sweep_d(const SweepArgs &A, int D, size_t smem, unsigned grid,
 }
 
 template <typename V, typename AT, int DIR, int D>
-static int launch_line(const SweepArgs &A, size_t smem, unsigned grid, cudaStream_t s)
+static int line_smem_attr(size_t smem)
 {
     static size_t attr = 0;  // benign race: setting the attribute twice is harmless
     if (smem > attr) {
@@ -1417,17 +1501,69 @@ static int launch_line(const SweepArgs &A, size_t smem, unsigned grid, cudaStrea
                                     (int)smem));
         attr = smem;
     }
+    return LSG_OK;
+}
+
+static cudaLaunchConfig_t line_config(unsigned grid, size_t smem, int csz, cudaStream_t s, cudaLaunchAttribute *at)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(32 * L1_WARPS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)csz;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+// Clusters of csz line CTAs that can be resident at once (0: none, or the query failed).
+template <typename V, typename AT, int DIR, int D>
+static int line_clusters(size_t smem, int csz)
+{
+    if (line_smem_attr<V, AT, DIR, D>(smem) != LSG_OK) return 0;
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = line_config((unsigned)csz, smem, csz, nullptr, at);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_sweep_line<V, AT, DIR, D>, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+// csz > 1: launched in clusters of csz CTAs (grid a multiple of csz).
+template <typename V, typename AT, int DIR, int D>
+static int launch_line(const SweepArgs &A, size_t smem, unsigned grid, int csz, cudaStream_t s)
+{
+    LSG_TRY((line_smem_attr<V, AT, DIR, D>(smem)));
     ::lsg::count_launch();
-    k_sweep_line<V, AT, DIR, D><<<grid, 32 * L1_WARPS, smem, s>>>(A);
+    if (csz <= 1) {
+        k_sweep_line<V, AT, DIR, D><<<grid, 32 * L1_WARPS, smem, s>>>(A);
+    } else {
+        cudaLaunchAttribute at[1];
+        const cudaLaunchConfig_t cfg = line_config(grid, smem, csz, s, at);
+        LSG_CK(cudaLaunchKernelEx(&cfg, k_sweep_line<V, AT, DIR, D>, A));
+    }
     LSG_CK(cudaGetLastError());
     return LSG_OK;
 }
 
 template <typename V, typename AT, int DIR>
-static int launch_line_d(const SweepArgs &A, int D, size_t smem, unsigned grid, cudaStream_t s)
+static int launch_line_d(const SweepArgs &A, int D, size_t smem, unsigned grid, int csz, cudaStream_t s)
 {
-    if (D == L1_D) return launch_line<V, AT, DIR, L1_D>(A, smem, grid, s);
-    return launch_line<V, AT, DIR, L1_DS>(A, smem, grid, s);
+    if (D == L1_D) return launch_line<V, AT, DIR, L1_D>(A, smem, grid, csz, s);
+    return launch_line<V, AT, DIR, L1_DS>(A, smem, grid, csz, s);
+}
+
+template <typename V, typename AT, int DIR>
+static int line_clusters_d(int D, size_t smem, int csz)
+{
+    if (D == L1_D) return line_clusters<V, AT, DIR, L1_D>(smem, csz);
+    return line_clusters<V, AT, DIR, L1_DS>(smem, csz);
 }
 
 template <typename AT>
@@ -1475,7 +1611,24 @@ static int sweeps_line(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done
     int dev = 0, nsm = 0;
     LSG_CK(cudaGetDevice(&dev));
     LSG_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const unsigned grid = (unsigned)std::min<long long>(wavefront_ctas(g, 1), nsm);
+    unsigned grid = (unsigned)std::min<long long>(wavefront_ctas(g, 1), nsm);
+    // 2D: clusters of line CTAs hand the values of each line to the next through
+    // distributed shared memory (one cluster group of csz lines at a time; rank 0 of a
+    // group still reads the previous group's last line from the output); enough
+    // clusters for the wavefront's busy lines plus one group
+    int csz = 1;
+    if (g.d == 2) {
+        for (int cs : {L1_CLUSTER, 4}) {
+            const long long ncl = (wavefront_ctas(g, 1) + cs - 1) / cs + 1;
+            if (g.nlines < 2LL * cs || ncl * cs > nsm) continue;
+            const int mf = line_clusters_d<V, AT, 1>(D, smf, cs), mb = line_clusters_d<V, AT, -1>(D, smb, cs);
+            if (std::min(mf, mb) >= ncl) {
+                csz = cs;
+                grid = (unsigned)(ncl * cs);
+                break;
+            }
+        }
+    }
     int slot;
     // forward: L y = r
     A.F = c->Lv;
@@ -1485,7 +1638,7 @@ static int sweeps_line(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done
     A.counter = c->counters + 1;
     LSG_TRY(prof_begin(c, PROF_SWEEP_L, s, &slot));
     LSG_TRY(launch_fill<AT>(ytmp, g.n, c->counters + 1, done, nsm, s));
-    LSG_TRY((launch_line_d<V, AT, 1>(A, D, smf, grid, s)));
+    LSG_TRY((launch_line_d<V, AT, 1>(A, D, smf, grid, csz, s)));
     LSG_TRY(prof_end(c, slot, s));
     // backward: U z = y (z is filled only now: it may be the same vector as r)
     A.F = c->Uv;
@@ -1495,7 +1648,7 @@ static int sweeps_line(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done
     A.counter = c->counters + 2;
     LSG_TRY(prof_begin(c, PROF_SWEEP_U, s, &slot));
     LSG_TRY(launch_fill<AT>(z, g.n, c->counters + 2, done, nsm, s));
-    LSG_TRY((launch_line_d<V, AT, -1>(A, D, smb, grid, s)));
+    LSG_TRY((launch_line_d<V, AT, -1>(A, D, smb, grid, csz, s)));
     LSG_TRY(prof_end(c, slot, s));
     return LSG_OK;
 }
