@@ -934,6 +934,7 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
     __shared__ long long s_line;
     __shared__ int s_issued;                   // chunks the producer issued (this line)
     __shared__ unsigned long long s_group;     // cluster mode: the group rank 0 claimed (all ones: stop)
+    __shared__ unsigned long long s_zero8;     // zero word for the finisher's factor-less lanes
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     // warp roles (warp w runs on SM sub-partition w % 4): the finisher alone on
     // sub-partition 0 (with two idle warps); the stale warps two per sub-partition 1-3,
@@ -954,6 +955,7 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
     const V *F = (const V *)A.F;
 
     if (threadIdx.x < 32) s_fown[threadIdx.x] = -1, s_fprev[threadIdx.x] = -1;
+    if (threadIdx.x == 0) s_zero8 = 0ull;
     __syncthreads();
     for (int t = threadIdx.x; t < nslot; t += blockDim.x) {
         const int s = DIR > 0 ? t : G.Sc + 1 + t;
@@ -1123,9 +1125,13 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
                 const int qj = s + j;
                 const bool in = j < K && qj >= 0 && qj < n1;
                 const unsigned ro = (unsigned)(qj & (D - 1)) * rowb;
-                fo = (in && fo_t >= 0) ? (AT)lds_val(a_fo + ro, V(0)) : AT(0);
-                fp = (in && fp_t >= 0) ? (AT)lds_val(a_fp + ro, V(0)) : AT(0);
-                if (DIR < 0) ri = in ? (AT)lds_val(a_ri + ro, V(0)) : AT(1);  // 1 / U(i,i), stored by the factorisation
+                // every lane loads, from a zero word where it has no factor: a conditional
+                // inline-asm load would be a divergent branch in the step loop
+                fo = (AT)lds_val((in && fo_t >= 0) ? a_fo + ro : smem_u32(&s_zero8), V(0));
+                fp = (AT)lds_val((in && fp_t >= 0) ? a_fp + ro : smem_u32(&s_zero8), V(0));
+                // 1 / U(i,i), stored by the factorisation (only lane 0's is used, and only at
+                // positions in the line)
+                if (DIR < 0) ri = (AT)lds_val(a_ri + ro, V(0));
             };
             auto load_T = [&](int s) -> bits_t {
                 return s >= 0 ? lds_vol(a_T + (unsigned)((s % L1_DT) * (int)sizeof(AT)), bits_t(0)) : bits_t(0);
@@ -1203,12 +1209,11 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
                     sts_vol(a_T + (unsigned)((s % L1_DT) * (int)sizeof(AT)), FB::v);
                     sts_val(a_Y + (unsigned)(i * (int)sizeof(AT)), yb);
                     st_release_cta(&s_prog, s + 1);
-                    // and to the output for the next lines (after the release: its fence does
-                    // not wait for this store)
-                    if (lane == 0) {
-                        if (fwd) st_cluster(a_next + (unsigned)(i * (int)sizeof(AT)), yb);
-                        st_final(out + i + (long long)n1 * line, yb);
-                    }
+                    // and to the next line's CTA and the output (after the release: its fence
+                    // does not wait for these stores); every lane stores the same value, one
+                    // transaction each, with no divergent branch
+                    if (fwd) st_cluster(a_next + (unsigned)(i * (int)sizeof(AT)), yb);
+                    st_final(out + i + (long long)n1 * line, yb);
                     if (more) ok = make_B(s + 1);
                 }
             }
