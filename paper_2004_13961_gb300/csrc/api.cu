@@ -105,7 +105,7 @@ static size_t footprint(const Geom &g, int precision, unsigned flags)
     size_t b = 2 * (size_t)g.Q * 8 + z.tab + 3 * z.grid + 2 * z.series + 2 * z.band + z.Lv + z.Uv +
                z.Mkeep + z.ws + 7 * z.vec + (size_t)g.n * 4 * 2 + 2 * z.lines + 64 + kRedBlocks * 16 +
                sizeof(PcgState);
-    if (precision != LSG_FP64) b += 6 * (size_t)g.n * 4 + 2 * (size_t)g.nq * 4 + 2 * z.vec + z.ws / 2;
+    if (precision != LSG_FP64) b += 6 * (size_t)g.n * 4 + 2 * (size_t)g.nq * 4 + 2 * z.vec + tc_ws_bytes(g, precision);
     b += tc_table_bytes(g, precision);
     // transient setup buffers: sample staging (2 grids) and the precontracted arrays
     size_t T1 = g.T + 1;
@@ -419,7 +419,12 @@ static int setup_impl(lsg_ctx **out, int d, int N, const int ta[3][3], const int
         else if (d == 3 && c->Waz == c->Way) c->Wa32z = c->Wa32y;
         ALLOC(c->e64, z.vec);
         ALLOC(c->u64, z.vec);
-        ALLOC(c->ws32, z.ws / 2);
+        ALLOC(c->ws32, tc_ws_bytes(g, precision));
+        // padding slots of the split fields are never written: they must read as zero
+        if (st == LSG_OK && cudaMemsetAsync(c->ws32, 0, tc_ws_bytes(g, precision), s) != cudaSuccess) {
+            record_cuda_error(cudaGetLastError(), "clearing the split-field workspace", __FILE__, __LINE__);
+            st = LSG_ERR_CUDA;
+        }
         ALLOC(c->tct, tc_table_bytes(g, precision));
     }
     // host samples are staged in temporary device arrays (one per distinct array)

@@ -125,7 +125,7 @@ struct lsg_ctx {
     // matrix-free product workspace
     double *ws;
     size_t ws_elems;
-    float *ws32;
+    float *ws32;            // mixed contexts: the split fields of the tensor-core product (tc_ws_bytes)
 
     // PCG vectors and reductions
     double *r, *z, *p, *wv, *xs, *fs, *ys;   // xs/fs/ys: staging for host arguments
@@ -167,6 +167,8 @@ int apply_K(lsg_ctx *c, const double *x, double *y, const int *done, cudaStream_
 int apply_K_tc(lsg_ctx *c, const float *x, float *y, const int *done, cudaStream_t s);
 int build_tc_tables(lsg_ctx *c, cudaStream_t s);
 size_t tc_table_bytes(const Geom &g, int precision);
+// the mixed form's split-field workspace (cleared once at set-up)
+size_t tc_ws_bytes(const Geom &g, int precision);
 int load_vector(lsg_ctx *c, const double *f, double *F, cudaStream_t s);
 int eval_grid(lsg_ctx *c, const double *u, double *vals, cudaStream_t s);
 int apply_Minv(lsg_ctx *c, const double *r, double *z, const int *done, cudaStream_t s);

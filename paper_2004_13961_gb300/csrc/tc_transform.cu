@@ -19,6 +19,9 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <cstring>
+
 #include "lsg_internal.cuh"
 
 namespace lsg {
@@ -27,10 +30,26 @@ constexpr int TC_BM = 128;      // rows of D per CTA (tensor-memory lanes)
 constexpr int TC_BN = 128;      // columns of D per CTA (tensor-memory columns)
 constexpr int TC_BK = 32;       // K elements per pipeline stage
 constexpr int TC_THREADS = 128;
-// two stages of A and B (hi and lo pieces each): 128 KB for TF32, 64 KB for
-// BF16, so at most three CTAs (3 x 128 tensor-memory columns) share an SM
+// pipeline stages of A and B (hi and lo pieces each): 3 x 64 KB for TF32, 6 x 32 KB
+// for BF16 (one CTA per SM either way)
 template <typename OP>
-constexpr size_t tc_smem() { return (size_t)2 * 4 * TC_BM * TC_BK * sizeof(OP) + 128; }
+constexpr int tc_stages() { return sizeof(OP) == 4 ? 3 : 6; }
+template <typename OP>
+constexpr size_t tc_smem() { return (size_t)tc_stages<OP>() * 4 * TC_BM * TC_BK * sizeof(OP) + 128; }
+
+// Operand arrays (the tables and the split fields) are stored tile by tile: each
+// tile of 128 rows x TC_BK columns is contiguous and already in the core-matrix order
+// the MMA reads from shared memory (8 rows x 16 bytes per core matrix, K-adjacent core
+// matrices 128 bytes apart, 8-row groups TC_BK * ES * 8 bytes apart), so that one bulk
+// copy moves a tile.  Element (r, k) of an array with nkb tiles per 128-row block:
+template <int ES>
+__host__ __device__ inline long long tc_tile_off(long long r, int k, int nkb)
+{
+    constexpr int EPC = 16 / ES, KC = TC_BK / EPC;  // elements per 16 bytes; 16-byte chunks per row
+    const int rr = (int)(r & 127), kk = k % TC_BK;
+    return ((r >> 7) * nkb + k / TC_BK) * (long long)(128 * TC_BK) + ((rr >> 3) * KC + kk / EPC) * (8 * EPC) +
+           (rr & 7) * EPC + kk % EPC;
+}
 
 template <typename OP>
 struct TcOp;
@@ -45,12 +64,21 @@ struct TcOp<__nv_bfloat16> {  // BF16: .kind::f16, K = 16 per instruction
     static constexpr int kmma = 16;
 };
 
+// Operands between contractions are kept split, as the next contraction reads B: a
+// field of L values is an array of L / Kn rows of Kn values (Kn = the next
+// contraction's K) padded to rup(Kn, TC_BK) columns and whole 128-row blocks, tiled as
+// above, hi pieces then lo pieces; padding is zero (the workspace is cleared once, and a
+// contraction writes a padding slot only with zero).
 struct TcTerm {
-    const void *A;    // [Mp][Kp] table (hi pieces) in the operand type, zero padded; lo pieces follow
-    const float *X;   // [N][K] FP32 field
+    const void *A;    // [Mp][Kp] table (hi pieces, tiled) in the operand type, zero padded; lo pieces follow
+    const void *B;    // [Np][Kp] field (hi pieces, tiled) in the operand type; lo pieces `blo` elements on
+    long long blo;
 };
 struct TcOut {
-    float *y;            // [M][N]
+    float *y;            // FP32 [M][N] output (the last contraction), or null
+    void *ys;            // else the split output, for a next contraction with K = Kn
+    long long ylo;       // elements from its hi pieces to its lo pieces
+    int Kn, Kpn;         // the next contraction's K and its padded row length
     const float *scale;  // optional [M][N] pointwise factor
     int nterm;
     TcTerm t[2];
@@ -161,27 +189,46 @@ __device__ __forceinline__ void tc_split<__nv_bfloat16>(float v, __nv_bfloat16 &
     lo = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
-// One 128 x 128 tile of D per CTA, K streamed through two shared-memory stages.
+__device__ __forceinline__ void tc_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_saddr(bar)), "r"(bytes) : "memory");
+}
+// one bulk copy global -> shared, completing on `bar` (both addresses 16-byte aligned)
+__device__ __forceinline__ void tc_bulk(void *sdst, const void *gsrc, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(tc_saddr(sdst)),
+        "l"(gsrc), "r"(bytes), "r"(tc_saddr(bar))
+        : "memory");
+}
+
+// One 128 x 128 tile of D per CTA.  One thread runs the pipeline: per K step it
+// moves the four tiles (A hi and lo, B hi and lo; both already split and tiled) into
+// a stage with bulk copies completing on the stage's `full` barrier, issues the
+// step's MMAs once they have landed, and refills the stage of the previous step once
+// that step's MMAs are done (tcgen05.commit on the stage's `mdone` barrier).
 template <typename OP>
 __global__ void __launch_bounds__(TC_THREADS) k_tc_gemm(const __grid_constant__ TcJob J)
 {
     if (J.done && *J.done) return;
     const TcOut &O = J.o[blockIdx.z];
     extern __shared__ __align__(1024) unsigned char smem[];
+    constexpr int S = tc_stages<OP>();
     constexpr int ES = (int)sizeof(OP);
-    constexpr int KC = TC_BK * ES / 16;             // 16-byte chunks per row and stage
-    constexpr int ABYTES = TC_BM * TC_BK * ES, BBYTES = TC_BN * TC_BK * ES;
-    constexpr int STAGE = 2 * (ABYTES + BBYTES);  // A hi, A lo, B hi, B lo
+    constexpr int KC = TC_BK * ES / 16;            // 16-byte chunks per row and stage
+    constexpr int TB = TC_BM * TC_BK * ES;         // bytes of one tile (TC_BN == TC_BM)
+    constexpr int STAGE = 4 * TB;                  // A hi, A lo, B hi, B lo
     constexpr uint32_t IDESC = tc_idesc(TcOp<OP>::fmt, TC_BM, TC_BN);
-    uint64_t *mbar = (uint64_t *)(smem + 2 * STAGE);
-    uint32_t *tslot = (uint32_t *)(mbar + 2);
+    static_assert(TC_BN == TC_BM, "A and B tiles have the same shape");
+    uint64_t *full = (uint64_t *)(smem + S * STAGE), *mdone = full + S;
+    uint32_t *tslot = (uint32_t *)(mdone + S);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * TC_BM;
-    const long long n0 = (long long)blockIdx.y * TC_BN;
+    const int mb = blockIdx.x, nbk = blockIdx.y;
+    const int m0 = mb * TC_BM;
+    const long long n0 = (long long)nbk * TC_BN;
 
     if (tid == 0) {
-        tc_mbar_init(&mbar[0]);
-        tc_mbar_init(&mbar[1]);
+        for (int i = 0; i < 2 * S; ++i) tc_mbar_init(&full[i]);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -195,73 +242,136 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_gemm(const __grid_constant__ 
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    const int nkt = (J.K + TC_BK - 1) / TC_BK;
+    const int nkt = J.Kp / TC_BK;  // K tiles
     const int total = nkt * O.nterm;
     bool ok = true;
-    for (int it = 0; it < total; ++it) {
-        const int s = it & 1;
-        unsigned char *sA = smem + s * STAGE, *sAl = sA + ABYTES, *sB = sAl + ABYTES, *sBl = sB + BBYTES;
-        // the MMAs that read this stage two iterations ago must be complete
-        if (it >= 2 && ok) ok = tc_wait(&mbar[s], (uint32_t)(((it >> 1) - 1) & 1), J.err);
-        const TcTerm tm = O.t[it / nkt];
-        const int k0 = (it % nkt) * TC_BK;
-        // A: rows m0.., K columns k0.. of the padded table, 16-byte chunks
-        const unsigned char *Ag = (const unsigned char *)tm.A;
-        const unsigned char *Agl = Ag + J.lo * ES;
-        for (int c = tid; c < TC_BM * KC; c += TC_THREADS) {
-            const int r = c / KC, kc = c % KC;
-            const size_t go = ((size_t)(m0 + r) * J.Kp + k0) * ES + kc * 16;
-            const int so = ((r >> 3) * KC + kc) * 128 + (r & 7) * 16;
-            *(uint4 *)(sA + so) = *(const uint4 *)(Ag + go);
-            *(uint4 *)(sAl + so) = *(const uint4 *)(Agl + go);
-        }
-        // B: rows n0.. of the field, converted to the operand type (zero outside)
-        for (int e = tid; e < TC_BN * TC_BK; e += TC_THREADS) {
-            const int r = e / TC_BK, k = e % TC_BK;
-            const long long n = n0 + r;
-            const int kk = k0 + k;
-            const float v = (n < J.N && kk < J.K) ? tm.X[n * J.K + kk] : 0.0f;
-            OP hi, lo;
-            tc_split<OP>(v, hi, lo);
-            const int so = ((r >> 3) * KC + ((k * ES) >> 4)) * 128 + (r & 7) * 16 + ((k * ES) & 15);
-            *(OP *)(sB + so) = hi;
-            *(OP *)(sBl + so) = lo;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
-        ok = __syncthreads_and(ok);
-        if (tid == 0 && ok) {
+    if (tid == 0) {
+        int issued = 0, consumed = 0, last = -1;
+        auto issue = [&](int k) {
+            const int st = k % S;
+            unsigned char *sp = smem + st * STAGE;
+            const TcTerm tm = O.t[k / nkt];
+            const int kb = k % nkt;
+            const OP *A = (const OP *)tm.A + ((long long)mb * nkt + kb) * (TC_BM * TC_BK);
+            const OP *B = (const OP *)tm.B + ((long long)nbk * nkt + kb) * (TC_BN * TC_BK);
+            tc_expect_tx(&full[st], 4u * TB);
+            tc_bulk(sp, A, TB, &full[st]);
+            tc_bulk(sp + TB, A + J.lo, TB, &full[st]);
+            tc_bulk(sp + 2 * TB, B, TB, &full[st]);
+            tc_bulk(sp + 3 * TB, B + tm.blo, TB, &full[st]);
+            ++issued;
+        };
+        for (int k = 0; k < S - 1 && k < total; ++k) issue(k);
+        for (int it = 0; it < total && ok; ++it) {
+            const int st = it % S;
+            ok = tc_wait(&full[st], (uint32_t)((it / S) & 1), J.err);
+            if (!ok) break;
+            consumed = it + 1;
             tc_fence_after();
+            const uint32_t sa = tc_saddr(smem + st * STAGE), sbo = (uint32_t)KC * 128u;
 #pragma unroll
             for (int j = 0; j < TC_BK / TcOp<OP>::kmma; ++j) {
-                const uint32_t sbo = (uint32_t)KC * 128u;
-                const uint64_t ah = tc_desc(tc_saddr(sA) + 256u * j, 128u, sbo);
-                const uint64_t al = tc_desc(tc_saddr(sAl) + 256u * j, 128u, sbo);
-                const uint64_t bh = tc_desc(tc_saddr(sB) + 256u * j, 128u, sbo);
-                const uint64_t bl = tc_desc(tc_saddr(sBl) + 256u * j, 128u, sbo);
+                const uint64_t ah = tc_desc(sa + 256u * j, 128u, sbo);
+                const uint64_t al = tc_desc(sa + TB + 256u * j, 128u, sbo);
+                const uint64_t bh = tc_desc(sa + 2 * TB + 256u * j, 128u, sbo);
+                const uint64_t bl = tc_desc(sa + 3 * TB + 256u * j, 128u, sbo);
                 tc_mma<OP>(tmem, ah, bh, IDESC, (it > 0 || j > 0) ? 1u : 0u);  // hi * hi
                 tc_mma<OP>(tmem, ah, bl, IDESC, 1u);                            // hi * lo
                 tc_mma<OP>(tmem, al, bh, IDESC, 1u);                            // lo * hi
             }
-            tc_commit(&mbar[s]);
+            tc_commit(&mdone[st]);
+            last = it;
+            // refill the stage of step it - 1 with step it + S - 1, once its MMAs are done
+            const int nx = it + S - 1;
+            if (nx < total) {
+                if (it >= 1) ok = tc_wait(&mdone[(it - 1) % S], (uint32_t)(((it - 1) / S) & 1), J.err);
+                if (ok) issue(nx);
+            }
         }
+        // every MMA must be complete before the tile is read or its memory reused (on an
+        // error too: the last commit covers every MMA issued before it), and so must every
+        // bulk copy issued
+        if (last >= 0 && !tc_wait(&mdone[last % S], (uint32_t)((last / S) & 1), J.err)) ok = false;
+        for (int k = consumed; k < issued; ++k) (void)tc_wait(&full[k % S], (uint32_t)((k / S) & 1), J.err);
+        if (last < total - 1) ok = false;
     }
-    // the last commit covers every MMA issued before it
-    if (ok) ok = tc_wait(&mbar[(total - 1) & 1], (uint32_t)(((total - 1) >> 1) & 1), J.err);
+    ok = __syncthreads_and(ok);
     tc_fence_after();
-    // epilogue: warp w owns tensor-memory lanes 32w..32w+31 = rows m0+32w+lane
-    const int m = m0 + 32 * warp + lane;
+    // epilogue: warp w owns tensor-memory lanes 32w..32w+31 = rows m0+32w+lane; the tile
+    // goes through shared memory (free now) so that the stores, and the reads of the
+    // pointwise factor, run along memory
+    float *tile = (float *)smem;  // [TC_BM][TC_BN + 1]
+    constexpr int TP = TC_BN + 1;
     for (int c0 = 0; c0 < TC_BN; c0 += 16) {
         uint32_t r[16];
         tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, r);
-        if (!ok || m >= J.M) continue;
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-            const long long n = n0 + c0 + jj;
-            if (n >= J.N) break;
-            float v = __uint_as_float(r[jj]);
-            const size_t o = (size_t)m * J.N + n;
-            if (O.scale) v *= O.scale[o];
-            O.y[o] = v;
+        for (int jj = 0; jj < 16; ++jj) tile[(32 * warp + lane) * TP + c0 + jj] = __uint_as_float(r[jj]);
+    }
+    __syncthreads();
+    OP *yh = (OP *)O.ys, *yl = yh + O.ylo;
+    const int nkbn = O.Kpn / TC_BK;  // K tiles of the next contraction
+    if (!ok) {
+    } else if (!O.y && J.N == O.Kn) {
+        // the output's rows are the next B's rows and its columns the next K: this tile
+        // fills whole next-B tiles (row block mb, K tiles n0 / TC_BK ..), written 16 bytes
+        // per thread in memory order, zero outside the field
+        constexpr int EPC = 16 / ES, PPT = TC_BM * TC_BK / EPC;
+        for (int t = 0; t < TC_BN / TC_BK; ++t) {
+            const int kb = (int)(n0 / TC_BK) + t;
+            if (kb >= nkbn) break;
+            const long long tb = ((long long)mb * nkbn + kb) * (TC_BM * TC_BK);
+            for (int p = tid; p < PPT; p += TC_THREADS) {
+                const int chunk = p >> 3, rr = ((chunk / KC) << 3) | (p & 7), cl = t * TC_BK + (chunk % KC) * EPC;
+                const int m = m0 + rr;
+                OP h[EPC], l[EPC];
+#pragma unroll
+                for (int e = 0; e < EPC; ++e) {
+                    const long long n = n0 + cl + e;
+                    float v = 0.0f;
+                    if (m < J.M && n < J.N) {
+                        v = tile[rr * TP + cl + e];
+                        if (O.scale) v *= O.scale[(size_t)m * J.N + n];
+                    }
+                    tc_split<OP>(v, h[e], l[e]);
+                }
+                uint4 vh, vl;
+                memcpy(&vh, h, 16);
+                memcpy(&vl, l, 16);
+                *(uint4 *)(yh + tb + (long long)p * EPC) = vh;
+                *(uint4 *)(yl + tb + (long long)p * EPC) = vl;
+            }
+        }
+    } else {
+        const long long n = n0 + tid;  // one column per thread
+        if (n < J.N) {
+            // general layout: flat index o = m N + n is row o / Kn, column o % Kn of the
+            // next B; from one row to the next o grows by N
+            const long long Kn = O.Kn, qN = J.N / Kn, rN = J.N % Kn;
+            const long long o0 = (long long)m0 * J.N + n;
+            long long row = o0 / Kn, col = o0 - (o0 / Kn) * Kn;
+            for (int rr = 0; rr < TC_BM; ++rr) {
+                const int m = m0 + rr;
+                if (m >= J.M) break;
+                const size_t o = (size_t)m * J.N + n;
+                float v = tile[rr * TP + tid];
+                if (O.scale) v *= O.scale[o];
+                if (O.y) {
+                    O.y[o] = v;
+                } else {
+                    const long long so = tc_tile_off<ES>(row, (int)col, nkbn);
+                    OP hi, lo;
+                    tc_split<OP>(v, hi, lo);
+                    yh[so] = hi;
+                    yl[so] = lo;
+                }
+                row += qN;
+                col += rN;
+                if (col >= Kn) {
+                    col -= Kn;
+                    ++row;
+                }
+            }
         }
     }
     tc_fence_before();
@@ -269,8 +379,24 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_gemm(const __grid_constant__ 
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
 }
 
+// The product's input field, split into the operand type in the layout the first
+// contraction reads (L values as L / Kn rows of Kn, tiled).
+template <typename OP>
+__global__ void k_tc_split(const float *x, long long L, int Kn, int Kpn, OP *hi, long long lo, const int *done)
+{
+    if (done && *done) return;
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < L; f += (long long)gridDim.x * blockDim.x) {
+        const long long row = f / Kn;
+        const long long o = tc_tile_off<(int)sizeof(OP)>(row, (int)(f - row * Kn), Kpn / TC_BK);
+        OP h, l;
+        tc_split<OP>(x[f], h, l);
+        hi[o] = h;
+        hi[lo + o] = l;
+    }
+}
+
 // ---- unfolded tables in the operand type -------------------------------------
-// Forward tables Fphi/Fdphi [2][MpF][KpF] (hi, lo): row q (node), column k
+// Forward tables Fphi/Fdphi [2][MpF][KpF] (hi, lo; tiled): row q (node), column k
 // (basis index); backward tables Bphi/Bdphi [2][MpB][KpB]: their transposes.  Built from the
 // parity-folded FP64 tables (first half of the nodes): for the mirrored node,
 // phi_k(-x) = (-1)^k phi_k(x) and phi'_k(-x) = (-1)^(k+1) phi'_k(x).
@@ -308,17 +434,20 @@ __global__ void k_tc_tables(int Q, int n1, int Qh, int QhP, int KP, const double
     OP ph, pl, dh, dl;
     tc_split<OP>((float)phi, ph, pl);
     tc_split<OP>((float)dphi, dh, dl);
+    // stored tiled (row q and column k forward, row k and column q backward)
+    constexpr int ES = (int)sizeof(OP);
     if (fwd) {
-        Fphi[idx] = ph;
-        Fphi[nF + idx] = pl;
-        Fdphi[idx] = dh;
-        Fdphi[nF + idx] = dl;
+        const long long o = tc_tile_off<ES>(q, k, KpF / TC_BK);
+        Fphi[o] = ph;
+        Fphi[nF + o] = pl;
+        Fdphi[o] = dh;
+        Fdphi[nF + o] = dl;
     } else {
-        const long long e = idx - nF;
-        Bphi[e] = ph;
-        Bphi[nB + e] = pl;
-        Bdphi[e] = dh;
-        Bdphi[nB + e] = dl;
+        const long long o = tc_tile_off<ES>(k, q, KpB / TC_BK);
+        Bphi[o] = ph;
+        Bphi[nB + o] = pl;
+        Bdphi[o] = dh;
+        Bdphi[nB + o] = dl;
     }
 }
 
@@ -358,6 +487,61 @@ int build_tc_tables(lsg_ctx *c, cudaStream_t s)
 }
 
 // ---- K x as a chain of tensor-core contractions -------------------------------
+// The split fields of the chain: (L, Kn) per buffer, L values as L / Kn rows of Kn.
+struct TcBufSpec {
+    long long L;
+    int Kn;
+};
+static int tc_buffers(const Geom &g, TcBufSpec *b)
+{
+    const long long Q = g.Q, n1 = g.n1;
+    const int q = (int)Q, n = (int)n1;
+    int k = 0;
+    if (g.d == 1) {
+        b[k++] = {n1, n};                        // x
+        b[k++] = {Q, q}, b[k++] = {Q, q};        // H, Gx
+    } else if (g.d == 2) {
+        b[k++] = {n1 * n1, n};                   // x
+        b[k++] = {Q * n1, n}, b[k++] = {Q * n1, n};                              // AP, AD
+        b[k++] = {Q * Q, q}, b[k++] = {Q * Q, q}, b[k++] = {Q * Q, q};           // H, Gy, Gx
+        b[k++] = {n1 * Q, q}, b[k++] = {n1 * Q, q};                              // P1, P2
+    } else {
+        b[k++] = {n1 * n1 * n1, n};                                              // x
+        b[k++] = {Q * n1 * n1, n}, b[k++] = {Q * n1 * n1, n};                    // A0, A1
+        for (int i = 0; i < 3; ++i) b[k++] = {Q * Q * n1, n};                    // B0, B1, B2
+        for (int i = 0; i < 4; ++i) b[k++] = {Q * Q * Q, q};                     // H, Gz, Gy, Gx
+        for (int i = 0; i < 3; ++i) b[k++] = {n1 * Q * Q, q};                    // Pa, Pb, Pc
+        b[k++] = {n1 * n1 * Q, q}, b[k++] = {n1 * n1 * Q, q};                    // Ra, Rc
+    }
+    return k;
+}
+// elements of one piece (hi or lo) of a split field: rows padded for the B tiles,
+// rows padded for the K steps, rounded to 256 bytes
+static long long tc_piece(const TcBufSpec &b, int es)
+{
+    const long long rows = rup((int)((b.L + b.Kn - 1) / b.Kn), TC_BN);
+    const long long e = rows * rup(b.Kn, TC_BK);
+    return (e * es + 255) / 256 * 256 / es;
+}
+
+size_t tc_ws_bytes(const Geom &g, int precision)
+{
+    if (precision == LSG_FP64) return 0;
+    const int es = precision == LSG_MIXED_TF32 ? 4 : 2;
+    TcBufSpec b[16];
+    const int nb = tc_buffers(g, b);
+    size_t t = 0;
+    for (int i = 0; i < nb; ++i) t += 2 * (size_t)tc_piece(b[i], es) * es;
+    return t;
+}
+
+template <typename OP>
+struct TcBuf {
+    OP *p;
+    long long lo;
+    int Kn, Kpn;
+};
+
 template <typename OP>
 struct TcBuilder {
     lsg_ctx *c;
@@ -399,15 +583,22 @@ struct TcBuilder {
         j.done = done;
         j.err = c->err;
     }
-    void out(float *y, const float *scale, const float *x0, int t0, const float *x1 = nullptr, int t1 = 0)
+    // one output: a split field for the next contraction (y null) or the FP32 result
+    void out(const TcBuf<OP> &dst, float *y, const float *scale, const TcBuf<OP> &x0, int t0,
+             const TcBuf<OP> *x1 = nullptr, int t1 = 0)
     {
         const bool f = isfwd;
         TcOut &o = j.o[j.nout++];
         o.y = y;
+        o.ys = y ? nullptr : (void *)dst.p;
+        o.ylo = dst.lo;
+        o.Kn = dst.Kn;
+        o.Kpn = dst.Kpn;
         o.scale = scale;
         o.nterm = x1 ? 2 : 1;
-        o.t[0] = TcTerm{f ? (const void *)tabF(t0) : (const void *)tabB(t0), x0};
-        o.t[1] = TcTerm{x1 ? (f ? (const void *)tabF(t1) : (const void *)tabB(t1)) : nullptr, x1};
+        o.t[0] = TcTerm{f ? (const void *)tabF(t0) : (const void *)tabB(t0), x0.p, x0.lo};
+        o.t[1] = TcTerm{x1 ? (f ? (const void *)tabF(t1) : (const void *)tabB(t1)) : nullptr, x1 ? x1->p : nullptr,
+                        x1 ? x1->lo : 0};
     }
     int launch(cudaStream_t s)
     {
@@ -429,72 +620,84 @@ static int apply_K_tc_t(lsg_ctx *c, const float *x, float *y, const int *done, c
 {
     const Geom &g = c->g;
     const long long Q = g.Q, n1 = g.n1;
-    float *ws = c->ws32;
     const float *Wa = c->Wa32, *Way = c->Wa32y, *Waz = c->Wa32z, *Wb = c->Wb32;  // W a_j per gradient term
+    TcBufSpec spec[16];
+    const int nb = tc_buffers(g, spec);
+    TcBuf<OP> B[16];
+    OP *p = (OP *)c->ws32;
+    for (int i = 0; i < nb; ++i) {
+        const long long e = tc_piece(spec[i], (int)sizeof(OP));
+        B[i] = TcBuf<OP>{p, e, spec[i].Kn, rup(spec[i].Kn, TC_BK)};
+        p += 2 * e;
+    }
+    const TcBuf<OP> none{nullptr, 0, 1, 1};
+    // the input field, split
+    {
+        const long long L = spec[0].L;
+        const unsigned blocks = (unsigned)std::min<long long>((L + 255) / 256, 4096);
+        ::lsg::count_launch();
+        k_tc_split<OP><<<blocks, 256, 0, s>>>(x, L, B[0].Kn, B[0].Kpn, B[0].p, B[0].lo, done);
+        LSG_CK(cudaGetLastError());
+    }
     TcBuilder<OP> T{c, {}, true};
     if (g.d == 1) {
-        float *H = ws, *Gx = ws + Q;
+        const TcBuf<OP> &X = B[0], &H = B[1], &Gx = B[2];
         T.fwd(1, done);
-        T.out(H, Wb, x, 0);
-        T.out(Gx, Wa, x, 1);
+        T.out(H, nullptr, Wb, X, 0);
+        T.out(Gx, nullptr, Wa, X, 1);
         LSG_TRY(T.launch(s));
         T.bwd(1, done);
-        T.out(y, nullptr, H, 0, Gx, 1);
+        T.out(none, y, nullptr, H, 0, &Gx, 1);
         return T.launch(s);
     }
     if (g.d == 2) {
-        float *AP = ws, *AD = ws + Q * n1;                              // [Q][n1]
-        float *H = ws + 2 * Q * n1, *Gy = H + Q * Q, *Gx = Gy + Q * Q;  // [Q][Q]
-        float *P1 = AP, *P2 = AD;                                       // [n1][Q]
+        const TcBuf<OP> &X = B[0], &AP = B[1], &AD = B[2], &H = B[3], &Gy = B[4], &Gx = B[5], &P1 = B[6], &P2 = B[7];
         T.fwd(n1, done);  // contract x
-        T.out(AP, nullptr, x, 0);
-        T.out(AD, nullptr, x, 1);
+        T.out(AP, nullptr, nullptr, X, 0);
+        T.out(AD, nullptr, nullptr, X, 1);
         LSG_TRY(T.launch(s));
         T.fwd(Q, done);  // contract y, pointwise W a / W b
-        T.out(H, Wb, AP, 0);
-        T.out(Gy, Way, AP, 1);
-        T.out(Gx, Wa, AD, 0);
+        T.out(H, nullptr, Wb, AP, 0);
+        T.out(Gy, nullptr, Way, AP, 1);
+        T.out(Gx, nullptr, Wa, AD, 0);
         LSG_TRY(T.launch(s));
         T.bwd(Q, done);  // back over x nodes
-        T.out(P1, nullptr, H, 0, Gx, 1);
-        T.out(P2, nullptr, Gy, 0);
+        T.out(P1, nullptr, nullptr, H, 0, &Gx, 1);
+        T.out(P2, nullptr, nullptr, Gy, 0);
         LSG_TRY(T.launch(s));
         T.bwd(n1, done);  // back over y nodes
-        T.out(y, nullptr, P1, 0, P2, 1);
+        T.out(none, y, nullptr, P1, 0, &P2, 1);
         return T.launch(s);
     }
-    float *A0 = ws, *A1 = ws + Q * n1 * n1;
-    float *B0 = ws + 2 * Q * n1 * n1, *B1 = B0 + Q * Q * n1, *B2 = B1 + Q * Q * n1;
-    float *F0 = B2 + Q * Q * n1, *F1 = F0 + Q * Q * Q, *F2 = F1 + Q * Q * Q, *F3 = F2 + Q * Q * Q;
-    float *H = F0, *Gz = F1, *Gy = F2, *Gx = F3;
+    const TcBuf<OP> &X = B[0], &A0 = B[1], &A1 = B[2], &B0 = B[3], &B1 = B[4], &B2 = B[5];
+    const TcBuf<OP> &H = B[6], &Gz = B[7], &Gy = B[8], &Gx = B[9], &Pa = B[10], &Pb = B[11], &Pc = B[12];
+    const TcBuf<OP> &Ra = B[13], &Rc = B[14];
     T.fwd(n1 * n1, done);
-    T.out(A0, nullptr, x, 0);
-    T.out(A1, nullptr, x, 1);
+    T.out(A0, nullptr, nullptr, X, 0);
+    T.out(A1, nullptr, nullptr, X, 1);
     LSG_TRY(T.launch(s));
     T.fwd(Q * n1, done);
-    T.out(B0, nullptr, A0, 0);
-    T.out(B1, nullptr, A0, 1);
-    T.out(B2, nullptr, A1, 0);
+    T.out(B0, nullptr, nullptr, A0, 0);
+    T.out(B1, nullptr, nullptr, A0, 1);
+    T.out(B2, nullptr, nullptr, A1, 0);
     LSG_TRY(T.launch(s));
     T.fwd(Q * Q, done);
-    T.out(H, Wb, B0, 0);
-    T.out(Gz, Waz, B0, 1);
-    T.out(Gy, Way, B1, 0);
-    T.out(Gx, Wa, B2, 0);
+    T.out(H, nullptr, Wb, B0, 0);
+    T.out(Gz, nullptr, Waz, B0, 1);
+    T.out(Gy, nullptr, Way, B1, 0);
+    T.out(Gx, nullptr, Wa, B2, 0);
     LSG_TRY(T.launch(s));
-    float *Pa = B0, *Pb = B1, *Pc = B2;
     T.bwd(Q * Q, done);
-    T.out(Pa, nullptr, H, 0, Gx, 1);
-    T.out(Pb, nullptr, Gy, 0);
-    T.out(Pc, nullptr, Gz, 0);
+    T.out(Pa, nullptr, nullptr, H, 0, &Gx, 1);
+    T.out(Pb, nullptr, nullptr, Gy, 0);
+    T.out(Pc, nullptr, nullptr, Gz, 0);
     LSG_TRY(T.launch(s));
-    float *Ra = A0, *Rc = A1;
     T.bwd(n1 * Q, done);
-    T.out(Ra, nullptr, Pa, 0, Pb, 1);
-    T.out(Rc, nullptr, Pc, 0);
+    T.out(Ra, nullptr, nullptr, Pa, 0, &Pb, 1);
+    T.out(Rc, nullptr, nullptr, Pc, 0);
     LSG_TRY(T.launch(s));
     T.bwd(n1 * n1, done);
-    T.out(y, nullptr, Ra, 0, Rc, 1);
+    T.out(none, y, nullptr, Ra, 0, &Rc, 1);
     return T.launch(s);
 }
 
