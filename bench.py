@@ -638,6 +638,20 @@ def run_profile_case(args):
     from paper_2004_13961_gb300 import workloads as W
     lsg.load()
     dev = torch.device("cuda", 0)
+    if args.profile_case == "n512-tf32-kx":
+        # three tensor-core products K x at the bench workload's size (2D N=512 T=8, TF32)
+        p = W.exp_2d_n512()
+        a, b = torch.tensor(p["a"], device=dev), torch.tensor(p["b"], device=dev)
+        ctx = lsg.Context(2, 512, 8, a, b, precision=lsg.MIXED_TF32)
+        g = torch.Generator(device=dev).manual_seed(4)
+        x = torch.randn(ctx.n, dtype=torch.float32, device=dev, generator=g)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            ctx.apply_A_lowp(x, y)
+        torch.cuda.synchronize()
+        print(json.dumps(dict(profile_case=args.profile_case, sum_abs=float(y.abs().sum()))), flush=True)
+        ctx.close()
+        return
     prec = {"n256-fp64": lsg.FP64, "n256-tf32": lsg.MIXED_TF32, "n256-bf16": lsg.MIXED_BF16}[args.profile_case]
     p = W.random_exp_problem(2, 256, 8, 1, 2, 3)
     a, b, f = (torch.tensor(p[k], device=dev) for k in ("a", "b", "f"))
@@ -662,8 +676,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-c3", action="store_true", help="skip the 3D N=128 FP64-vs-mixed line")
-    ap.add_argument("--profile-case", choices=["n256-fp64", "n256-tf32", "n256-bf16"], default=None,
-                    help="run one 2D N=256 T=8 setup + solve and exit (the small case of the ncu captures)")
+    ap.add_argument("--profile-case", choices=["n256-fp64", "n256-tf32", "n256-bf16", "n512-tf32-kx"], default=None,
+                    help="run one 2D N=256 T=8 setup + solve (or three 2D N=512 tensor-core products) and exit: "
+                         "the small cases of the ncu captures")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)

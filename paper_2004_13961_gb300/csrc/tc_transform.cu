@@ -26,16 +26,16 @@
 
 namespace lsg {
 
-constexpr int TC_BM = 128;      // rows of D per CTA (tensor-memory lanes)
-constexpr int TC_BN = 128;      // columns of D per CTA (tensor-memory columns)
+constexpr int TC_BM = 128;      // rows of D per CTA (tensor-memory lanes); rows of a stored tile
+constexpr int TC_BN = 64;       // columns of D per CTA (tensor-memory columns): half a stored tile of B
 constexpr int TC_BK = 32;       // K elements per pipeline stage
 constexpr int TC_THREADS = 128;
-// pipeline stages of A and B (hi and lo pieces each): 3 x 64 KB for TF32, 6 x 32 KB
+// pipeline stages of A and B (hi and lo pieces each): 4 x 48 KB for TF32, 7 x 24 KB
 // for BF16 (one CTA per SM either way)
 template <typename OP>
-constexpr int tc_stages() { return sizeof(OP) == 4 ? 3 : 6; }
+constexpr int tc_stages() { return sizeof(OP) == 4 ? 4 : 7; }
 template <typename OP>
-constexpr size_t tc_smem() { return (size_t)tc_stages<OP>() * 4 * TC_BM * TC_BK * sizeof(OP) + 128; }
+constexpr size_t tc_smem() { return (size_t)tc_stages<OP>() * 2 * (TC_BM + TC_BN) * TC_BK * sizeof(OP) + 128; }
 
 // Operand arrays (the tables and the split fields) are stored tile by tile: each
 // tile of 128 rows x TC_BK columns is contiguous and already in the core-matrix order
@@ -216,10 +216,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_gemm(const __grid_constant__ 
     constexpr int S = tc_stages<OP>();
     constexpr int ES = (int)sizeof(OP);
     constexpr int KC = TC_BK * ES / 16;            // 16-byte chunks per row and stage
-    constexpr int TB = TC_BM * TC_BK * ES;         // bytes of one tile (TC_BN == TC_BM)
-    constexpr int STAGE = 4 * TB;                  // A hi, A lo, B hi, B lo
+    constexpr int TB = TC_BM * TC_BK * ES;         // bytes of a stored tile (A)
+    constexpr int TBB = TC_BN * TC_BK * ES;        // bytes of a B tile: the first or second half of a stored one
+    constexpr int STAGE = 2 * (TB + TBB);          // A hi, A lo, B hi, B lo
     constexpr uint32_t IDESC = tc_idesc(TcOp<OP>::fmt, TC_BM, TC_BN);
-    static_assert(TC_BN == TC_BM, "A and B tiles have the same shape");
+    static_assert(TC_BM % TC_BN == 0, "B tiles are equal parts of a stored tile");
     uint64_t *full = (uint64_t *)(smem + S * STAGE), *mdone = full + S;
     uint32_t *tslot = (uint32_t *)(mdone + S);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -252,13 +253,17 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_gemm(const __grid_constant__ 
             unsigned char *sp = smem + st * STAGE;
             const TcTerm tm = O.t[k / nkt];
             const int kb = k % nkt;
+            // B rows n0.. are part nbk % (TC_BM / TC_BN) of the stored tile of row block
+            // n0 / TC_BM: a contiguous run of the tile (its 8-row groups are in row order)
+            constexpr int NP = TC_BM / TC_BN;
             const OP *A = (const OP *)tm.A + ((long long)mb * nkt + kb) * (TC_BM * TC_BK);
-            const OP *B = (const OP *)tm.B + ((long long)nbk * nkt + kb) * (TC_BN * TC_BK);
-            tc_expect_tx(&full[st], 4u * TB);
+            const OP *B = (const OP *)tm.B + ((long long)(nbk / NP) * nkt + kb) * (TC_BM * TC_BK) +
+                          (nbk % NP) * (TC_BN * TC_BK);
+            tc_expect_tx(&full[st], 2u * (TB + TBB));
             tc_bulk(sp, A, TB, &full[st]);
             tc_bulk(sp + TB, A + J.lo, TB, &full[st]);
-            tc_bulk(sp + 2 * TB, B, TB, &full[st]);
-            tc_bulk(sp + 3 * TB, B + tm.blo, TB, &full[st]);
+            tc_bulk(sp + 2 * TB, B, TBB, &full[st]);
+            tc_bulk(sp + 2 * TB + TBB, B + tm.blo, TBB, &full[st]);
             ++issued;
         };
         for (int k = 0; k < S - 1 && k < total; ++k) issue(k);
@@ -274,7 +279,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_gemm(const __grid_constant__ 
                 const uint64_t ah = tc_desc(sa + 256u * j, 128u, sbo);
                 const uint64_t al = tc_desc(sa + TB + 256u * j, 128u, sbo);
                 const uint64_t bh = tc_desc(sa + 2 * TB + 256u * j, 128u, sbo);
-                const uint64_t bl = tc_desc(sa + 3 * TB + 256u * j, 128u, sbo);
+                const uint64_t bl = tc_desc(sa + 2 * TB + TBB + 256u * j, 128u, sbo);
                 tc_mma<OP>(tmem, ah, bh, IDESC, (it > 0 || j > 0) ? 1u : 0u);  // hi * hi
                 tc_mma<OP>(tmem, ah, bl, IDESC, 1u);                            // hi * lo
                 tc_mma<OP>(tmem, al, bh, IDESC, 1u);                            // lo * hi
@@ -300,13 +305,19 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_gemm(const __grid_constant__ 
     // epilogue: warp w owns tensor-memory lanes 32w..32w+31 = rows m0+32w+lane; the tile
     // goes through shared memory (free now) so that the stores, and the reads of the
     // pointwise factor, run along memory
-    float *tile = (float *)smem;  // [TC_BM][TC_BN + 1]
+    float *tile = (float *)smem;  // [TC_BM][TC_BN + 1], the pointwise factor applied
     constexpr int TP = TC_BN + 1;
+    const int mrow = m0 + 32 * warp + lane;
     for (int c0 = 0; c0 < TC_BN; c0 += 16) {
         uint32_t r[16];
         tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, r);
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) tile[(32 * warp + lane) * TP + c0 + jj] = __uint_as_float(r[jj]);
+        for (int jj = 0; jj < 16; ++jj) {
+            float v = __uint_as_float(r[jj]);
+            const long long n = n0 + c0 + jj;
+            if (O.scale && mrow < J.M && n < J.N) v *= O.scale[(size_t)mrow * J.N + n];
+            tile[(32 * warp + lane) * TP + c0 + jj] = v;
+        }
     }
     __syncthreads();
     OP *yh = (OP *)O.ys, *yl = yh + O.ylo;
@@ -329,10 +340,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_gemm(const __grid_constant__ 
                 for (int e = 0; e < EPC; ++e) {
                     const long long n = n0 + cl + e;
                     float v = 0.0f;
-                    if (m < J.M && n < J.N) {
-                        v = tile[rr * TP + cl + e];
-                        if (O.scale) v *= O.scale[(size_t)m * J.N + n];
-                    }
+                    if (m < J.M && n < J.N) v = tile[rr * TP + cl + e];
                     tc_split<OP>(v, h[e], l[e]);
                 }
                 uint4 vh, vl;
@@ -343,19 +351,21 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_gemm(const __grid_constant__ 
             }
         }
     } else {
-        const long long n = n0 + tid;  // one column per thread
+        // RS threads per column, on alternate rows
+        constexpr int RS = TC_THREADS / TC_BN;
+        const int r0 = tid / TC_BN;
+        const long long n = n0 + tid % TC_BN;
         if (n < J.N) {
             // general layout: flat index o = m N + n is row o / Kn, column o % Kn of the
-            // next B; from one row to the next o grows by N
-            const long long Kn = O.Kn, qN = J.N / Kn, rN = J.N % Kn;
-            const long long o0 = (long long)m0 * J.N + n;
+            // next B; from one of this thread's rows to the next o grows by RS N
+            const long long Kn = O.Kn, qN = RS * J.N / Kn, rN = RS * J.N % Kn;
+            const long long o0 = (long long)(m0 + r0) * J.N + n;
             long long row = o0 / Kn, col = o0 - (o0 / Kn) * Kn;
-            for (int rr = 0; rr < TC_BM; ++rr) {
+            for (int rr = r0; rr < TC_BM; rr += RS) {
                 const int m = m0 + rr;
                 if (m >= J.M) break;
                 const size_t o = (size_t)m * J.N + n;
-                float v = tile[rr * TP + tid];
-                if (O.scale) v *= O.scale[o];
+                const float v = tile[rr * TP + (int)(n - n0)];
                 if (O.y) {
                     O.y[o] = v;
                 } else {
@@ -519,7 +529,7 @@ static int tc_buffers(const Geom &g, TcBufSpec *b)
 // rows padded for the K steps, rounded to 256 bytes
 static long long tc_piece(const TcBufSpec &b, int es)
 {
-    const long long rows = rup((int)((b.L + b.Kn - 1) / b.Kn), TC_BN);
+    const long long rows = rup((int)((b.L + b.Kn - 1) / b.Kn), TC_BM);
     const long long e = rows * rup(b.Kn, TC_BK);
     return (e * es + 255) / 256 * 256 / es;
 }
