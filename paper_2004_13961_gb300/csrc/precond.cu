@@ -14,6 +14,8 @@
 
 #include <algorithm>
 
+#include <mutex>
+
 #include "lsg_internal.cuh"
 #include "stencil.cuh"
 
@@ -174,6 +176,13 @@ __global__ void k_level_scatter(StencilGeo G, int *cursor, int *order)
 // blocking); a step whose row was not ready at prefetch time waits for it and
 // copies it then.  A finished row stores 1 / U(r,r) in the pad slot SU-1.
 constexpr int ILU_MAX_WARPS = 8;
+#ifndef ILU_LEVELS
+// Rows in flight of the 2D factorisation, in wavefront levels' worth of rows: measured on a
+// GB300, 8 and 16 levels slowed the N=512 factorisation 5x and 2.6x (a row's elimination
+// overlaps far more levels than its last steps suggest), 48 cost 3 % there and made the
+// 256 set-ups of the batched form (N = 32..256 on 8 streams) 27 % faster.
+#define ILU_LEVELS 48
+#endif
 
 struct IluSmem {
     size_t off, smask, ord, warps, per_warp, total;
@@ -448,12 +457,37 @@ static int launch_ilu0_d(lsg_ctx *c, const StencilGeo &G, int nsm, cudaStream_t 
     const IluSmem one = ilu_layout(G.S, G.SU, D, (int)sizeof(V), 1);
     if (one.total > budget) return LSG_ERR_ARG;  // stencil too wide for a shared-memory row
     int nw = (int)std::min<size_t>(ILU_MAX_WARPS, 1 + (budget - one.total) / one.per_warp);
+    long long ctas = 0;
+    if (G.d == 2) {
+        // rows in flight: about n1/(w+1) rows per wavefront level times ILU_LEVELS; more
+        // warps only spin on rows far ahead, and a grid that fills the GPU keeps the
+        // factorisations of other problems (batched and served solves on other streams)
+        // from running beside it.  Spread over the SMs: the fewest warps per CTA that
+        // reach every SM.
+        const long long warps = ((long long)(G.n1 + G.w) / (G.w + 1) + 2) * ILU_LEVELS;
+        if (warps < (long long)nsm * 2 * nw) {
+            nw = (int)std::max<long long>(1, std::min<long long>(nw, (warps + nsm - 1) / nsm));
+            ctas = (warps + nw - 1) / nw;
+        }
+    }
     const size_t smem = ilu_layout(G.S, G.SU, D, (int)sizeof(V), nw).total;
-    LSG_CK(cudaFuncSetAttribute(k_ilu0<V, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    LSG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ilu0<V, D>, 32 * nw, smem));
-    if (per_sm < 1) return LSG_ERR_ARG;
-    long long ctas = std::min<long long>((long long)nsm * per_sm, (G.n + nw - 1) / nw);
+    {
+        // the attribute only grows: set-ups on other host threads may be launching with more
+        static std::mutex mu;
+        static size_t attr = 0;
+        std::lock_guard<std::mutex> lk(mu);
+        if (smem > attr) {
+            LSG_CK(cudaFuncSetAttribute(k_ilu0<V, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr = smem;
+        }
+    }
+    if (ctas == 0) {
+        int per_sm = 0;
+        LSG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ilu0<V, D>, 32 * nw, smem));
+        if (per_sm < 1) return LSG_ERR_ARG;
+        ctas = std::min<long long>((long long)nsm * per_sm, (G.n + nw - 1) / nw);
+    }
+    ctas = std::min<long long>(ctas, (G.n + nw - 1) / nw);
     ::lsg::count_launch();
     k_ilu0<V, D><<<(unsigned)ctas, 32 * nw, smem, s>>>(G, (V *)c->Lv, (V *)c->Uv, c->order, c->rowflag,
                                                         c->counters, c->err);
