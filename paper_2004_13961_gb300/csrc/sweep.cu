@@ -874,17 +874,37 @@ __device__ __forceinline__ bool poll_global(const AT *p, AT &val, const volatile
 
 // The finisher's rare slow path: poll the stale part and (2D/3D) the previous
 // line's value until both are final.  Kept out of line so that the step loop
-// holds no loop of its own.
+// holds no loop of its own; the operands travel by value (an address taken would
+// keep them in local memory on every step: measured 8 % of the sweep).
 template <typename AT>
-__device__ __noinline__ bool poll_operands(const AT *pT, const AT *pP, AT *Tv, AT *yp, const volatile int *abort_flag,
-                                           int *err, long long budget)
+struct FinOps {
+    typename Fill<AT>::bits t, p;
+    int good;
+};
+template <typename AT>
+__device__ __noinline__ FinOps<AT> poll_operands(const AT *pT, const AT *pP, FinOps<AT> o, const volatile int *abort_flag,
+                                                 int *err, long long budget)
 {
-    AT a, b = AT(0);
-    const bool good =
-        poll_value(pT, a, abort_flag, err, budget) && (pP == nullptr || poll_value(pP, b, abort_flag, err, budget));
-    *Tv = a;
-    if (pP != nullptr) *yp = b;
-    return good;
+    using bits_t = typename Fill<AT>::bits;
+    bool good = true;
+    const long long t0 = clock64();
+    for (int it = 0; good; ++it) {
+        const bool needT = o.t == Fill<AT>::v, needP = pP != nullptr && o.p == Fill<AT>::v;
+        if (!needT && !needP) break;
+        if (needT) o.t = *reinterpret_cast<const volatile bits_t *>(pT);
+        if (needP) o.p = *reinterpret_cast<const volatile bits_t *>(pP);
+        if (it >= 256) __nanosleep(16);
+        if ((it & 15) == 15) {
+            if (*abort_flag) {
+                good = false;
+            } else if (clock64() - t0 > budget) {
+                set_err(err, DERR_TIMEOUT);
+                good = false;
+            }
+        }
+    }
+    o.good = __all_sync(0xffffffffu, good) ? 1 : 0;
+    return o;
 }
 
 // Bounded wait for an mbarrier phase that also gives up when the CTA aborts.
@@ -1175,13 +1195,15 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
             // an operand that is not final yet (rare) is polled outside the hot loop's code
             AT Bv = 0;
             auto make_B = [&](int s) -> bool {
-                AT Tv = FB::val(tb), yp = FB::val(pb);
                 if (__any_sync(FULL, tb == FB::v || pb == FB::v)) {
-                    if (!poll_operands(&sT[s % L1_DT], G.d >= 2 ? &sy[prevoff + (DIR > 0 ? s : n1 - 1 - s)] : nullptr,
-                                       &Tv, &yp, &s_abort, A.err, A.budget))
-                        return false;
+                    const FinOps<AT> o =
+                        poll_operands(&sT[s % L1_DT], G.d >= 2 ? &sy[prevoff + (DIR > 0 ? s : n1 - 1 - s)] : nullptr,
+                                      FinOps<AT>{tb, pb, 1}, &s_abort, A.err, A.budget);
+                    if (!o.good) return false;
+                    tb = o.t;
+                    pb = o.p;
                 }
-                Bv = fma(-fp, yp, (j == 0) ? Tv : AT(0));
+                Bv = fma(-fp, FB::val(pb), (j == 0) ? FB::val(tb) : AT(0));
                 return true;
             };
             if (ok && n1 > 0) ok = make_B(0);
