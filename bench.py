@@ -228,7 +228,8 @@ def run_batched(lsg, W, torch, dev, world, count=256, precision=None, threads=8)
         for idx in range(k, count, threads):
             p = probs[idx]
             a, b, f = dev_in[idx]
-            c = lsg.Context(2, p["N"], p["T"], a, b, allow_breakdown=True, precision=precision, stream=st)
+            c = lsg.Context(2, p["N"], p["T"], a, b, allow_breakdown=True, precision=precision, stream=st,
+                            shared_gpu=True)
             if c.status == lsg.ERR_ILU_BREAKDOWN:  # ILU(0) of this M does not exist: counted, not solved
                 c.close()
                 out.append((idx, None, None))

@@ -81,6 +81,11 @@ enum lsg_precision {
 #define LSG_SETUP_AUTOTUNE 4u /* when the committed tile table has no entry for (d, N, Q), time the
                                  tile variants of the FP64 contractions of K x at setup and keep
                                  the fastest (lsg_autotune_transforms) */
+#define LSG_SETUP_SHARED_GPU 16u /* the context is set up while other work runs on the same GPU
+                                    (many problems at once, as the batched and served forms): the
+                                    ILU(0) factorisation of a 2D M runs on a grid sized by its
+                                    wavefront instead of one that fills the GPU, so that several
+                                    factorisations overlap; the factors are the same (bitwise) */
 
 /* lsg_export items (host output; sizes from lsg_export_count) */
 enum lsg_export_item {

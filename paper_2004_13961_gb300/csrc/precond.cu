@@ -177,9 +177,10 @@ __global__ void k_level_scatter(StencilGeo G, int *cursor, int *order)
 // copies it then.  A finished row stores 1 / U(r,r) in the pad slot SU-1.
 constexpr int ILU_MAX_WARPS = 8;
 #ifndef ILU_LEVELS
-// Rows in flight of the 2D factorisation, in wavefront levels' worth of rows: measured on a
-// GB300, 8 and 16 levels slowed the N=512 factorisation 5x and 2.6x (a row's elimination
-// overlaps far more levels than its last steps suggest), 48 cost 3 % there and made the
+// Rows in flight of a 2D factorisation set up beside other work (LSG_SETUP_SHARED_GPU), in
+// wavefront levels' worth of rows: measured on a GB300, 8 and 16 levels slowed the N=512
+// factorisation 5x and 2.6x (a row's elimination overlaps far more levels than its last steps
+// suggest), 48 cost 3 % there (a lone N=256 factorisation 54 %: 13.6 -> 20.9 ms) and made the
 // 256 set-ups of the batched form (N = 32..256 on 8 streams) 27 % faster.
 #define ILU_LEVELS 48
 #endif
@@ -458,7 +459,7 @@ static int launch_ilu0_d(lsg_ctx *c, const StencilGeo &G, int nsm, cudaStream_t 
     if (one.total > budget) return LSG_ERR_ARG;  // stencil too wide for a shared-memory row
     int nw = (int)std::min<size_t>(ILU_MAX_WARPS, 1 + (budget - one.total) / one.per_warp);
     long long ctas = 0;
-    if (G.d == 2) {
+    if (G.d == 2 && (c->flags & LSG_SETUP_SHARED_GPU)) {
         // rows in flight: about n1/(w+1) rows per wavefront level times ILU_LEVELS; more
         // warps only spin on rows far ahead, and a grid that fills the GPU keeps the
         // factorisations of other problems (batched and served solves on other streams)

@@ -63,7 +63,8 @@ static void run_one(lsg_server *S, Pending &p, lsg_result &res)
     }
     const lsg_request &q = p.req;
     lsg_ctx *ctx = nullptr;
-    int st = lsg_setup(&ctx, q.d, q.N, q.T, q.Q, p.a.data(), p.b.data(), q.precision, (lsg_stream_t)s);
+    int st = lsg_setup_ex(&ctx, q.d, q.N, q.T, q.Q, p.a.data(), p.b.data(), q.precision, LSG_SETUP_SHARED_GPU,
+                          (lsg_stream_t)s);
     if (st == LSG_OK) {
         const long long n = lsg_query(ctx, LSG_Q_UNKNOWNS);
         // F and u live on the device (stream-ordered allocations from the pool)

@@ -24,6 +24,7 @@ SETUP_KEEP_M = 1
 SETUP_PROFILE = 2
 SETUP_AUTOTUNE = 4
 SETUP_CONST_PRECOND = 8
+SETUP_SHARED_GPU = 16
 
 EXPORT_GAUSS_X, EXPORT_GAUSS_W, EXPORT_AHAT, EXPORT_BHAT = 0, 1, 2, 3
 EXPORT_BAND_S, EXPORT_BAND_M, EXPORT_M, EXPORT_LU = 4, 5, 6, 7
@@ -209,7 +210,7 @@ class Context:
     """An lsg_ctx: tables, coefficient samples, M's ILU(0) factors and workspaces."""
 
     def __init__(self, d, N, T, a, b, Q=None, precision=FP64, keep_M=False, stream=None, allow_breakdown=False,
-                 profile=False, autotune=False, ta=None, tb=None, const_precond=False):
+                 profile=False, autotune=False, ta=None, tb=None, const_precond=False, shared_gpu=False):
         """A context for lsg_setup_ex (one coefficient a, one degree T), or -- when `a` is a list
         of d per-direction coefficients or the degrees ta (d x d: ta[j][i] of a_j in direction
         i) and tb (d) are given -- for lsg_setup_problem (T unused then)."""
@@ -220,7 +221,7 @@ class Context:
         self.precision = precision
         h = ctypes.c_void_p(0)
         flags = (SETUP_KEEP_M if keep_M else 0) | (SETUP_PROFILE if profile else 0) | (SETUP_AUTOTUNE if autotune else 0) \
-            | (SETUP_CONST_PRECOND if const_precond else 0)
+            | (SETUP_CONST_PRECOND if const_precond else 0) | (SETUP_SHARED_GPU if shared_gpu else 0)
         if isinstance(a, (list, tuple)) or ta is not None or tb is not None:
             alist = list(a) if isinstance(a, (list, tuple)) else [a] * d
             ta = [[T] * d for _ in range(d)] if ta is None else ta

@@ -4,6 +4,10 @@
   conditional WHILE node on the device; a profiled context runs the same kernels from
   a host loop.  Both must give bitwise the same iterate and iteration count (the
   kernels and their reduction orders are the same), matching the oracle.
+* A context set up with LSG_SETUP_SHARED_GPU (the factorisation on a grid sized by its
+  wavefront, for set-ups beside other work) has bitwise the same ILU(0) factors and
+  solve as one set up alone (the elimination order within a row is fixed; only which
+  warp takes which row changes).
 * Every tile shape the autotuner may choose gives K x to the oracle's 1e-11 bar, for
   each contraction of the 1D, 2D and 3D products (ragged tiles: odd Q, n1 not a
   multiple of any tile); the autotuner returns valid choices and the tuned product
@@ -100,3 +104,17 @@ def test_every_tile_shape_matches_oracle(lsg, case):
     assert info["status"] == 0
     c2.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("N", [64, 160])
+def test_shared_gpu_setup_gives_the_same_factors_and_solve(lsg, N):
+    p = W.random_exp_problem(2, N, 8, 31, 32, 33)
+    a, b, f = cuda(p["a"]), cuda(p["b"]), cuda(p["f"])
+    c1 = lsg.Context(2, N, 8, a, b)
+    c2 = lsg.Context(2, N, 8, a, b, shared_gpu=True)
+    assert np.array_equal(c1.export(lsg.EXPORT_LU), c2.export(lsg.EXPORT_LU))
+    u1, i1 = c1.pcg_solve(c1.load_vector(f), rtol=1e-12)
+    u2, i2 = c2.pcg_solve(c2.load_vector(f), rtol=1e-12)
+    assert i1["iters"] == i2["iters"] and np.array_equal(u1.cpu().numpy(), u2.cpu().numpy())
+    c1.close()
+    c2.close()
