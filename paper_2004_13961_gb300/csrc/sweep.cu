@@ -668,7 +668,8 @@ constexpr int L1_WARPS = 12;             // finisher, six stale warps, TMA produ
 constexpr int L1_CLUSTER = 8;            // 2D: lines per cluster group (one per CTA)
 constexpr int L1_D = 32;                 // factor ring depth (rows); rows D further ahead are prefetched to L2
 constexpr int L1_CH = 4;                 // rows per ring barrier (the finisher checks one per L1_CH positions)
-constexpr int L1_DS = 8;                 // ring depth where 32 rows do not fit (3D rows)
+constexpr int L1_DM = 16;                // ring depth where 32 rows do not fit (3D FP64 rows of T <= 4)
+constexpr int L1_DS = 8;                 // ... where 16 do not fit either
 constexpr int L1_FB = 16;                // finisher steps per block (ring waits at block starts)
 
 template <typename AT>
@@ -1583,6 +1584,7 @@ template <typename V, typename AT, int DIR>
 static int launch_line_d(const SweepArgs &A, int D, size_t smem, unsigned grid, int csz, cudaStream_t s)
 {
     if (D == L1_D) return launch_line<V, AT, DIR, L1_D>(A, smem, grid, csz, s);
+    if (D == L1_DM) return launch_line<V, AT, DIR, L1_DM>(A, smem, grid, csz, s);
     return launch_line<V, AT, DIR, L1_DS>(A, smem, grid, csz, s);
 }
 
@@ -1590,6 +1592,7 @@ template <typename V, typename AT, int DIR>
 static int line_clusters_d(int D, size_t smem, int csz)
 {
     if (D == L1_D) return line_clusters<V, AT, DIR, L1_D>(smem, csz);
+    if (D == L1_DM) return line_clusters<V, AT, DIR, L1_DM>(smem, csz);
     return line_clusters<V, AT, DIR, L1_DS>(smem, csz);
 }
 
@@ -1687,7 +1690,9 @@ static int sweeps(lsg_ctx *c, const AT *r, AT *z, AT *ytmp, const int *done, cud
     const size_t budget = 210 * 1024;
     if ((g.d == 3 || g.Sc <= 32 * SW_KS) && g.w <= 31) {
         const int vs = (int)sizeof(V), as = (int)sizeof(AT);
-        for (int D : {L1_D, L1_DS}) {
+        // the deepest ring that fits: the finisher's window (K = 8 from 16 rows, 4 from 8)
+        // is the slack the stale warps have to finish a row
+        for (int D : {L1_D, L1_DM, L1_DS}) {
             const size_t smf = line_layout(g.d, g.n1, g.w, D, g.SL, vs, g.Sc, as).total;
             const size_t smb = line_layout(g.d, g.n1, g.w, D, g.SU, vs, g.Sc, as).total;
             if (std::max(smf, smb) <= budget) return sweeps_line<V, AT>(c, r, z, ytmp, done, s, D, smf, smb);
