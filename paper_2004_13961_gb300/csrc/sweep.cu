@@ -644,9 +644,10 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
 // two of its positions, so a position costs a full FP64 reduction (~1 us) and a
 // 2D sweep, a chain of about n1 (w+1) + n1 positions, keeps only ~n1/(w+1) lines
 // busy at a time.  Here a CTA owns one line:
-//   * L1_NS stale warps compute T_q = r_q - (every term of row q except the K
-//     newest values of the own line and the K newest of the previous line),
-//     position q by warp q % L1_NS, K positions ahead of the finisher;
+//   * L1_NS stale warps (L1_NS3 in 3D) compute T_q = r_q - (every term of row q
+//     except the K newest values of the own line and the K newest of the previous
+//     line), position q by the warp of index q modulo their count, K positions
+//     ahead of the finisher;
 //   * the finisher holds the window of the next K positions in its lanes
 //     (lane j: position s+j) and applies each new value -- y_{s-1} of the own
 //     line, y'_{s+w} of the previous one -- to the whole window with one
@@ -662,9 +663,13 @@ __global__ void __launch_bounds__(32 * (SW_MAXB + SW_HELP), 1) k_sweep(const __g
 //     values from the output the same way, through L1.
 // Lines are claimed in sweep order, so a CTA only waits for lines claimed
 // earlier by running CTAs; every wait is bounded and reports LSG_ERR_TIMEOUT.
-constexpr int L1_NS = 6;                 // stale warps
+constexpr int L1_NS = 6;                 // stale warps in 1D/2D
+constexpr int L1_NS3 = 9;                // ... in 3D, where their sums (other planes' values read through L1) bound the step
 constexpr int L1_DT = 32;                // ring of stale results (positions)
-constexpr int L1_WARPS = 12;             // finisher, six stale warps, TMA producer, two loaders, two idle
+// warps per CTA (a template parameter): 12 in 1D/2D (finisher, six stale warps, TMA producer, two
+// loaders, two idle), 16 in 3D (three more stale warps: at 512 threads the register cap of 128
+// per thread slowed the 2D finisher's step by 16 %, while 3D gains 16 %)
+constexpr int L1_WARPS2 = 12, L1_WARPS3 = 16;
 constexpr int L1_CLUSTER = 8;            // 2D: lines per cluster group (one per CTA)
 constexpr int L1_D = 32;                 // factor ring depth (rows); rows D further ahead are prefetched to L2
 constexpr int L1_CH = 4;                 // rows per ring barrier (the finisher checks one per L1_CH positions)
@@ -926,8 +931,8 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t *bar, unsigned parity, con
     }
 }
 
-template <typename V, typename AT, int DIR, int D>
-__global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_constant__ SweepArgs A)
+template <typename V, typename AT, int DIR, int D, int NW>
+__global__ void __launch_bounds__(32 * NW, 1) k_sweep_line(const __grid_constant__ SweepArgs A)
 {
     if (A.done && *A.done) return;
     using FB = Fill<AT>;
@@ -935,7 +940,8 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int NB = D / L1_CH;  // ring barriers, one per chunk of L1_CH rows
     static_assert(D % L1_CH == 0, "ring depth must be a multiple of the chunk");
-    static_assert(L1_NS == 6, "stale warps sit on sub-partitions 1-3, two each");
+    static_assert(L1_NS == 6 && L1_NS3 == 9 && (NW == L1_WARPS2 || NW == L1_WARPS3),
+                  "stale warps sit on sub-partitions 1-3, two or three each");
     const StencilGeo G = A.G;
     const int n1 = G.n1, w = G.w, RL = A.RL, nslot = G.Sc, K = A.K;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -963,14 +969,16 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
     // polls up to eight lines without pause: beside the finisher it slowed the
     // backward sweep's step by 12 %)
     enum { R_FIN, R_STALE, R_PROD, R_NEAR, R_FAR, R_IDLE };
-    const int role = wid == 0 ? R_FIN : (wid == 4 || wid == 8) ? R_IDLE : wid == 9 ? R_PROD : wid == 10 ? R_NEAR
-                   : wid == 11 ? R_FAR : R_STALE;
+    // stale warps: 1, 2, 3, 5, 6, 7 (index 0-5) and, with 16 warps (3D), 13, 14, 15 (index 6-8)
+    const int ns = NW == L1_WARPS3 ? L1_NS3 : L1_NS;
+    const int sw = wid < 4 ? wid - 1 : wid < 8 ? wid - 2 : wid - 7;  // stale warp index (R_STALE)
+    const int role = wid == 0 ? R_FIN : (wid == 4 || wid == 8 || wid == 12) ? R_IDLE : wid == 9 ? R_PROD
+                   : wid == 10 ? R_NEAR : wid == 11 ? R_FAR : sw < ns ? R_STALE : R_IDLE;
     // cluster mode (2D, launched in clusters): CTA `crank` of a cluster takes line
     // csz g + crank of the group g that rank 0 claims, and stores each value it finishes
     // into the previous-line row of CTA crank + 1 as well
     const unsigned csz = cluster_size(), crank = cluster_rank();
     const bool clu = csz > 1;
-    const int sw = wid < 4 ? wid - 1 : wid - 2;  // stale warp index (R_STALE)
     const AT *rhs = (const AT *)A.rhs;
     AT *out = (AT *)A.out;
     const V *F = (const V *)A.F;
@@ -1245,7 +1253,7 @@ __global__ void __launch_bounds__(32 * L1_WARPS, 1) k_sweep_line(const __grid_co
             // T_q = r_q - S_q, S_q every term of row q but the window's: own-line
             // positions < q-K and previous-line positions <= q+w-K are final once the
             // finisher has done q-K positions and line v-1 is staged that far
-            for (int q = sw; q < n1 && ok; q += L1_NS) {
+            for (int q = sw; q < n1 && ok; q += ns) {
                 ok = wait_ge(&s_prog, q - K, &s_abort, A.err, A.budget) &&
                      wait_ge(&s_near, min(max(0, q + w - K + 1), n1), &s_abort, A.err, A.budget) &&
                      wait_ge(&s_near2, min(q + w + 1, n1), &s_abort, A.err, A.budget) &&
@@ -1520,23 +1528,24 @@ static int launch_sweep_d(const SweepArgs &A, int D, size_t smem, unsigned grid,
     return launch_sweep<V, AT, DIR, 4>(A, smem, grid, s);
 }
 
-template <typename V, typename AT, int DIR, int D>
+template <typename V, typename AT, int DIR, int D, int NW>
 static int line_smem_attr(size_t smem)
 {
     static size_t attr = 0;  // benign race: setting the attribute twice is harmless
     if (smem > attr) {
-        LSG_CK(cudaFuncSetAttribute(k_sweep_line<V, AT, DIR, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        LSG_CK(cudaFuncSetAttribute(k_sweep_line<V, AT, DIR, D, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
         attr = smem;
     }
     return LSG_OK;
 }
 
-static cudaLaunchConfig_t line_config(unsigned grid, size_t smem, int csz, cudaStream_t s, cudaLaunchAttribute *at)
+static cudaLaunchConfig_t line_config(unsigned grid, int nw, size_t smem, int csz, cudaStream_t s,
+                                      cudaLaunchAttribute *at)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(32 * L1_WARPS);
+    cfg.blockDim = dim3(32 * nw);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1552,40 +1561,47 @@ static cudaLaunchConfig_t line_config(unsigned grid, size_t smem, int csz, cudaS
 template <typename V, typename AT, int DIR, int D>
 static int line_clusters(size_t smem, int csz)
 {
-    if (line_smem_attr<V, AT, DIR, D>(smem) != LSG_OK) return 0;
+    if (line_smem_attr<V, AT, DIR, D, L1_WARPS2>(smem) != LSG_OK) return 0;
     cudaLaunchAttribute at[1];
-    const cudaLaunchConfig_t cfg = line_config((unsigned)csz, smem, csz, nullptr, at);
+    const cudaLaunchConfig_t cfg = line_config((unsigned)csz, L1_WARPS2, smem, csz, nullptr, at);
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_sweep_line<V, AT, DIR, D>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, k_sweep_line<V, AT, DIR, D, L1_WARPS2>, &cfg) != cudaSuccess) {
         (void)cudaGetLastError();
         return 0;
     }
     return n;
 }
 
-// csz > 1: launched in clusters of csz CTAs (grid a multiple of csz).
-template <typename V, typename AT, int DIR, int D>
+// csz > 1: launched in clusters of csz CTAs (grid a multiple of csz; 2D only, NW = L1_WARPS2).
+template <typename V, typename AT, int DIR, int D, int NW>
 static int launch_line(const SweepArgs &A, size_t smem, unsigned grid, int csz, cudaStream_t s)
 {
-    LSG_TRY((line_smem_attr<V, AT, DIR, D>(smem)));
+    LSG_TRY((line_smem_attr<V, AT, DIR, D, NW>(smem)));
     ::lsg::count_launch();
     if (csz <= 1) {
-        k_sweep_line<V, AT, DIR, D><<<grid, 32 * L1_WARPS, smem, s>>>(A);
+        k_sweep_line<V, AT, DIR, D, NW><<<grid, 32 * NW, smem, s>>>(A);
     } else {
         cudaLaunchAttribute at[1];
-        const cudaLaunchConfig_t cfg = line_config(grid, smem, csz, s, at);
-        LSG_CK(cudaLaunchKernelEx(&cfg, k_sweep_line<V, AT, DIR, D>, A));
+        const cudaLaunchConfig_t cfg = line_config(grid, NW, smem, csz, s, at);
+        LSG_CK(cudaLaunchKernelEx(&cfg, k_sweep_line<V, AT, DIR, D, NW>, A));
     }
     LSG_CK(cudaGetLastError());
     return LSG_OK;
 }
 
+template <typename V, typename AT, int DIR, int NW>
+static int launch_line_dw(const SweepArgs &A, int D, size_t smem, unsigned grid, int csz, cudaStream_t s)
+{
+    if (D == L1_D) return launch_line<V, AT, DIR, L1_D, NW>(A, smem, grid, csz, s);
+    if (D == L1_DM) return launch_line<V, AT, DIR, L1_DM, NW>(A, smem, grid, csz, s);
+    return launch_line<V, AT, DIR, L1_DS, NW>(A, smem, grid, csz, s);
+}
+// 3D: 16 warps (nine stale); 1D/2D: 12
 template <typename V, typename AT, int DIR>
 static int launch_line_d(const SweepArgs &A, int D, size_t smem, unsigned grid, int csz, cudaStream_t s)
 {
-    if (D == L1_D) return launch_line<V, AT, DIR, L1_D>(A, smem, grid, csz, s);
-    if (D == L1_DM) return launch_line<V, AT, DIR, L1_DM>(A, smem, grid, csz, s);
-    return launch_line<V, AT, DIR, L1_DS>(A, smem, grid, csz, s);
+    if (A.G.d == 3) return launch_line_dw<V, AT, DIR, L1_WARPS3>(A, D, smem, grid, csz, s);
+    return launch_line_dw<V, AT, DIR, L1_WARPS2>(A, D, smem, grid, csz, s);
 }
 
 template <typename V, typename AT, int DIR>
